@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""SAFR per-frame reconstruction benchmark (GB300, sm_103a).
+
+Workload: the MORFEO-like frame: 39 m aperture, 80x80 pupil samples
+zero-padded to a 256x256 grid, 6 LGS (90 km, 2 arcmin ring) + 3 NGS
+(1.3 arcmin), 9 layers 0-16 km, FP32, batch 1, synthetic von Karman
+wavefronts (seeded).  One step = one frame through safr_reconstruct (pad +
+row FFT, column FFT + apply + inverse column FFT, inverse row FFT + resample
++ store).  The L2 cache (129 MB) is flushed by writing a 256 MB buffer before
+every timed frame, so B (21 MB) streams from HBM each frame.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl safr|reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs its own replica
+(frame-parallel, no collective on the data path) and rank 0 prints the line.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SAFR frames/s & p99 latency (MORFEO-like, FP32) vs FP64 oracle, % roofline"
+UNIT = "frames/s"
+WORKLOAD = "morfeo-256"
+FLUSH_BYTES = 256 << 20
+REF_BUDGET_S = 120.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="safr", choices=["safr", "reference"])
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def config_block(g):
+    return {"workload": WORKLOAD, "grid": g["M"], "pupil": g["P"], "lgs": int(np.sum(g["kind"] == 1)),
+            "ngs": int(np.sum(g["kind"] == 0)), "layers": len(g["h"]), "batch": 1,
+            "precision": "fp32", "l2": "flushed before every timed frame (256 MB write)"}
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) timing
+# ----------------------------------------------------------------------------
+def oracle_frames(geom, frames, budget_s, max_frames):
+    import oracle
+    oracle.build()
+    pl = oracle.OraclePlan(geom)
+    t0 = time.perf_counter()
+    n = 0
+    outs = {}
+    while n < max_frames:
+        outs[n % len(frames)] = pl.reconstruct(frames[n % len(frames)])
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n, dt, oracle.threads(), outs
+
+
+def run_reference(args):
+    from paper_2510_19542_gb300 import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    g = synth.config(2)
+    frames = [synth.frame(g, seed=100 + i) for i in range(2)]
+    import oracle
+    oracle.build()
+    pl = oracle.OraclePlan(g)
+    for i in range(min(args.warmup, 1)):
+        pl.reconstruct(frames[i % 2])
+    t0 = time.perf_counter()
+    done = 0
+    for i in range(args.steps):
+        pl.reconstruct(frames[i % 2])
+        done += 1
+        if time.perf_counter() - t0 > REF_BUDGET_S:
+            break
+    dt = time.perf_counter() - t0
+    val = done / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": done, "steps_requested": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / done, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic von Karman frames (seeded)", "config": config_block(g),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{done} full frames of the workload (FP64 oracle: naive DFT2, "
+                                       "Jacobi-SVD B precomputed once, untimed); warm-up "
+                                       f"{min(args.warmup, 1)} frame; steps stop after {REF_BUDGET_S:.0f} s"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def run_safr(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2510_19542_gb300 import safr, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    g = synth.config(2)
+    frames_np = [synth.frame(g, seed=100 + i) for i in range(8)]
+
+    # CPU baseline first (rank 0, N = 1): the oracle as it stands on the host cores
+    cpu, ref_layers = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n, dt, cores, ref_layers = oracle_frames(g, frames_np, args.cpu_sample_s, 64)
+        cpu = {"value": n / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n} full frames of the workload in {dt:.1f} s (FP64 oracle, naive DFT2; its "
+                         "Jacobi-SVD B precompute untimed)"}
+
+    plan = safr.Plan(g, device=local)
+    stream = torch.cuda.current_stream(dev)
+    frames = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in frames_np]
+    layers = plan.empty_layers()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    launches = safr.safr_launches_per_frame(plan.handle)
+    info = plan.info
+
+    def one(i, trace):
+        flush.fill_(float(i & 7))
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        safr.safr_reconstruct(plan.handle, frames[i % len(frames)], layers, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        ph = safr.safr_trace_read(plan.handle) if trace else None
+        return s.elapsed_time(e), ph
+
+    safr.safr_trace(plan.handle, True)
+    for i in range(args.warmup):
+        one(i, True)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    lat, phases = [], []
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        ms, ph = one(i, True)
+        lat.append(ms)
+        phases.append(ph)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(np.sum(lat))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    status = safr.safr_get_status(plan.handle)
+
+    # end to end through the public host-buffer entry point (pinned memory)
+    safr.safr_trace(plan.handle, False)
+    hin = [torch.from_numpy(f.astype(np.float32)).pin_memory() for f in frames_np]
+    hout = torch.empty((info["L"], info["M"], info["M"]), dtype=torch.float32).pin_memory()
+    for i in range(min(args.warmup, 5)):
+        safr.safr_reconstruct_host(plan.handle, hin[i % 8], hout, stream=stream)
+    e2e_ms = 0.0
+    for i in range(args.steps):
+        flush.fill_(float(i & 7))
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        safr.safr_reconstruct_host(plan.handle, hin[i % 8], hout, stream=stream)
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # the last timed frame against the FP64 oracle
+    rel_l2 = None
+    if ref_layers:
+        fi = (args.steps - 1) % len(frames)
+        if fi not in ref_layers:
+            fi = min(ref_layers)
+            safr.safr_reconstruct(plan.handle, frames[fi], layers, stream=stream)
+        else:
+            safr.safr_reconstruct(plan.handle, frames[fi], layers, stream=stream)
+        torch.cuda.synchronize(dev)
+        got = layers.double().cpu().numpy()
+        rel_l2 = float(np.linalg.norm(got - ref_layers[fi]) / np.linalg.norm(ref_layers[fi]))
+
+    if rank == 0:
+        ph = np.array(phases)  # [steps][3]
+        ph_mean = ph.mean(axis=0).tolist()
+        M, Mh = info["M"], info["M"] // 2
+        sumLG = info["L"] * info["G"]
+        b_bytes = M * Mh * sumLG * 8                  # algorithmic B: half spectrum, no Nyquist column
+        in_bytes = info["G"] * info["P"] ** 2 * 4
+        out_bytes = info["L"] * M * M * 4
+        frame_bytes = b_bytes + in_bytes + out_bytes
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        k2_s = ph_mean[1] * 1e-3
+        achieved = b_bytes / k2_s / 1e9
+        traffic = None
+        try:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+                traffic = json.load(f).get(WORKLOAD, {}).get("k_cols_apply")
+        except (OSError, ValueError):
+            traffic = None
+        lat_sorted = sorted(lat)
+        value = world * args.steps / (total_ms * 1e-3)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic von Karman frames (seeded), FP32", "config": config_block(g),
+            "latency_ms": {"p50": lat_sorted[len(lat) // 2],
+                           "p99": lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                           "mean": total_ms / args.steps},
+            "phases_ms": {"rows_forward": ph_mean[0], "cols_apply": ph_mean[1], "rows_inverse": ph_mean[2]},
+            "frame_roofline": {"bytes": frame_bytes, "achieved_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
+                               "peak_gbs": hbm, "frac": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9 / hbm},
+            "roofline": {"kernel": "k_cols_apply", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes": b_bytes},
+            "clocks": clk, "gpu_launches": launches * args.steps, "device_status": status,
+            "rel_l2_vs_oracle": rel_l2,
+            "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
+                    "ms_per_step": e2e_ms / args.steps},
+            "wall_s_timed_region": wall,
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_safr(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

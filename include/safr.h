@@ -1,0 +1,208 @@
+/*
+ * safr.h -- C ABI of the GB300 (sm_103a) SAFR library.
+ *
+ * SAFR (Singular value-based Atmospheric tomography with Fourier domain
+ * Regularization, arXiv 2510.19542) reconstructs L turbulence layers from G
+ * guide-star wavefronts.  Per frame (Algorithm 1, "hard real-time"):
+ *
+ *     d_g    = DFT2(Psi_g)                       g = 1..G
+ *     b_l(n) = sum_g B_lg(n) d_g(n)             every frequency n, l = 1..L
+ *     Phi_l  = IDFT2(b_l)                         l = 1..L
+ *
+ * with DFT2 unnormalised and IDFT2 carrying 1/M^2 (Section 3.2).  B is the
+ * block-diagonal-in-frequency matrix of Eq. (sparseM), precomputed once per
+ * geometry (Algorithm 2, "soft real-time"):
+ *
+ *     A_n[g][l] = s_l(n) exp(i pi n.(alpha_g h_l) / (c_l T))     (Section 3.1)
+ *     s_l(n)    = gamma_l^{1/2} / c_l (1 + tau_l |n|^2)^{-beta/2}, tau_l = pi^2/(c_l T)^2
+ *     B_n       = diag(s(n)) R_alpha(A_n),  R_alpha = V g_alpha(Sigma^T) U^H,
+ *     g_alpha(s)= s / (s^2 + alpha)                                   (Tikhonov)
+ *
+ * Mixed LGS + NGS asterisms use split tomography (Section 3.3, Algorithm 3):
+ * the tip/tilt of each LGS wavefront is removed, the LGS group (c_l = 1 -
+ * h_l/h_LGS) and the NGS group (c_l = 1, regularisation alpha_TT) are
+ * reconstructed separately and the layers are added.
+ *
+ * Conventions (all arrays row-major, C order):
+ *   - a wavefront Psi_g is P x P pupil samples, first index p <-> x, second
+ *     q <-> y; it is zero-extended (Section 2) into the periodic M x M grid at
+ *     offset o = (M-P)/2 on both axes;
+ *   - the grid pitch is delta = 2T/M (Section 3.2); layer l of an LGS group is
+ *     natively sampled at pitch c_l*delta (x^l_p = c_l x_p);
+ *   - frequencies with |n_x| or |n_y| = M/2 (the Nyquist row and column of an
+ *     even grid) are not reconstructed: B is zero there, which keeps the
+ *     output real (the paper's symmetric truncation assumes odd M = 2m+1).
+ *
+ * Ownership: the plan owns B, its workspaces and its staging buffers (device
+ * memory allocated in safr_plan_create).  The caller owns every buffer passed
+ * to safr_reconstruct.  All device work is ordered on the caller's stream.
+ *
+ * Errors: argument errors are returned synchronously and nothing is launched.
+ * Errors found on the device are recorded in the plan's sticky status word,
+ * read by safr_get_status.  No call ever traps or spins without a bound.
+ */
+#ifndef SAFR_H
+#define SAFR_H
+
+#include <cuda_runtime_api.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct safr_plan_s *safr_plan_t;
+
+typedef enum {
+    SAFR_OK = 0,
+    SAFR_ERR_INVALID_ARG = 1,      /* null pointer, bad size, bad geometry          */
+    SAFR_ERR_UNSUPPORTED_SIZE = 2, /* M not a power of two in [8, 1024], L or G too large */
+    SAFR_ERR_MISALIGNED = 3,       /* a device pointer not 16-byte aligned          */
+    SAFR_ERR_NOT_PRECOMPUTED = 4,  /* safr_reconstruct before safr_precompute       */
+    SAFR_ERR_OOM = 5,              /* cudaMalloc failed in safr_plan_create         */
+    SAFR_ERR_CUDA = 6,             /* a CUDA runtime call failed (no device, launch) */
+    SAFR_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up            */
+    SAFR_ERR_DEVICE = 8            /* a device-side check failed (see safr_get_status) */
+} safr_status;
+
+enum { SAFR_NGS = 0, SAFR_LGS = 1 };                           /* guide-star kind          */
+enum { SAFR_FP32 = 0, SAFR_FP16_STORAGE = 1, SAFR_FP64 = 2 };  /* precision                */
+enum { SAFR_NATIVE = 0, SAFR_METRIC = 1 };                     /* output grid              */
+
+/* Limits of one plan. */
+#define SAFR_MAX_M 1024
+#define SAFR_MAX_L 64
+#define SAFR_MAX_G 32       /* stars per plan                   */
+#define SAFR_MAX_GROUP_G 16 /* stars per group (LGS or NGS)     */
+
+/* Warning bits of safr_plan_info.warnings. */
+#define SAFR_WARN_CONTAINMENT 1 /* c_l Omega_A + alpha_g h_l is not inside c_l Omega_T (Section 2) */
+
+/*
+ * Telescope, asterism and atmosphere (Section 2).  Arrays are read during
+ * safr_plan_create only (copied).
+ */
+typedef struct {
+    int M;                 /* periodic grid size: power of two, 8 <= M <= 1024            */
+    int P;                 /* pupil samples across, 1 <= P <= M                           */
+    double pitch_m;        /* grid pitch delta = 2T/M in metres (T = M delta / 2)          */
+    double diameter_m;     /* pupil diameter D (annulus mask, removeTT only); <= 0: square */
+    double obstruction;    /* central obstruction as a fraction of D                      */
+    int L;                 /* number of layers, 1 <= L <= SAFR_MAX_L                      */
+    const double *h_m;     /* [L] layer heights, ascending, 0 <= h_l < h_lgs_m             */
+    const double *cn2;     /* [L] layer weights gamma_l > 0; normalised to sum 1 here      */
+    int G;                 /* number of guide stars, 1 <= G <= SAFR_MAX_G                 */
+    const double *dir_x;   /* [G] direction vectors alpha_g^x (Section 2: (ax, ay, 1) points at the star) */
+    const double *dir_y;   /* [G] alpha_g^y                                               */
+    const int *kind;       /* [G] SAFR_NGS or SAFR_LGS                                    */
+    double h_lgs_m;        /* sodium-layer height h_LGS (about 90 km)                     */
+    double alpha;          /* Tikhonov parameter of the LGS group, or of the single group */
+    double alpha_tt;       /* Tikhonov parameter of the NGS (tip-tilt star) group of a mixed plan */
+    double beta;           /* Sobolev smoothness beta >= 0                                */
+    int precision;         /* SAFR_FP32, SAFR_FP16_STORAGE or SAFR_FP64                   */
+    int output_grid;       /* SAFR_NATIVE or SAFR_METRIC (mixed plans need SAFR_METRIC)    */
+    int remove_tt;         /* mixed plans: remove LGS tip/tilt (Algorithm 3, line 3)      */
+} safr_geometry;
+
+typedef struct {
+    int M, P, L, G;
+    int ngroups;            /* 1 or 2 (LGS group first)                            */
+    int group_kind[2];      /* SAFR_LGS / SAFR_NGS                                 */
+    int group_G[2];         /* stars per group                                    */
+    size_t b_bytes;         /* bytes of B on the device                           */
+    size_t workspace_bytes; /* bytes of the inter-pass workspaces                 */
+    size_t in_bytes;        /* bytes of one frame of wavefronts                   */
+    size_t out_bytes;       /* bytes of one frame of layers                       */
+    int warnings;           /* SAFR_WARN_* bits                                   */
+    int precomputed;        /* 1 after safr_precompute                            */
+} safr_plan_info;
+
+/*
+ * Validate the geometry (Section 2: ascending heights below h_LGS, weights
+ * gamma_l > 0; P <= M), split the stars into an LGS and an NGS group
+ * (Section 3.3), derive c_l, the per-(star, layer) shifts alpha_g h_l /
+ * (c_l delta) and the resample tables, and allocate B and the workspaces on
+ * `cuda_device`.  On success *out is a new plan; on failure *out is NULL and
+ * nothing stays allocated.  A mixed plan with SAFR_NATIVE output is rejected.
+ */
+safr_status safr_plan_create(const safr_geometry *geom, int cuda_device, safr_plan_t *out);
+
+/*
+ * Algorithm 2: compute B for every stored frequency of every group on the
+ * GPU in FP64 (stored in FP32, or FP64 for SAFR_FP64).  The regularised
+ * inverse is evaluated as diag(s) A^H (A A^H + alpha I)^{-1}, which equals
+ * diag(s) V g_alpha(Sigma^T) U^H for the Tikhonov filter (Section 3.1).
+ * Asynchronous on `stream`; re-run it whenever alpha, gamma or the asterism
+ * changes (the soft real-time step of Section 3.2).
+ */
+safr_status safr_precompute(safr_plan_t plan, cudaStream_t stream);
+
+/*
+ * Algorithm 1 (plus removeTT and the group sum of Algorithm 3 for mixed
+ * plans) on device buffers.  Asynchronous on `stream`, no host
+ * synchronisation, no allocation.
+ *
+ *   d_wavefronts [G][P][P]: float (SAFR_FP32), __half (SAFR_FP16_STORAGE) or
+ *                double (SAFR_FP64), stars in the geometry's order.
+ *   d_in_scales  [G] float or NULL: SAFR_FP16_STORAGE only; Psi_g = value * scale_g
+ *                (NULL means 1).
+ *   d_layers     [L][M][M]: float, __half or double.  Layer l is sampled at
+ *                pitch c_l*delta (SAFR_NATIVE, single group) or delta (SAFR_METRIC).
+ *   d_out_scales [L] float: SAFR_FP16_STORAGE only (required there);
+ *                Phi_l = value * scale_l, scale_l a power of two chosen from the
+ *                layer's energy (Parseval).
+ * Every pointer must be 16-byte aligned device memory.
+ */
+safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const float *d_in_scales,
+                             void *d_layers, float *d_out_scales, cudaStream_t stream);
+
+/*
+ * End-to-end form of safr_reconstruct for host buffers: copies the frame from
+ * `h_wavefronts` (and `h_in_scales`) to plan-owned device staging buffers,
+ * reconstructs, copies the layers (and scales) back to `h_layers` /
+ * `h_out_scales`, and synchronises `stream` before returning.  Page-locked
+ * host memory makes the copies asynchronous DMA; pageable memory also works.
+ */
+safr_status safr_reconstruct_host(safr_plan_t plan, const void *h_wavefronts, const float *h_in_scales,
+                                  void *h_layers, float *h_out_scales, cudaStream_t stream);
+
+/* Sticky device-side status of the plan (synchronises the plan's device). */
+safr_status safr_get_status(safr_plan_t plan);
+
+/* Sizes, groups and warnings of a plan (host only, no synchronisation). */
+safr_status safr_get_plan_info(safr_plan_t plan, safr_plan_info *info);
+
+/*
+ * Copy group `group`'s B to host memory as complex FP64 pairs (re, im),
+ * layout [k][l][g][j] for k in [0, M/2), l in [0, L), g over the group's stars
+ * in geometry order, j in [0, M): entry B_lg at frequency (j, k), the n(j),
+ * n(k) labels of Section 3.2.  `dst` holds 2*(M/2)*L*G_group*M doubles.
+ * Synchronises the plan's device.  For inspection and tests.
+ */
+safr_status safr_copy_B(safr_plan_t plan, int group, double *dst);
+
+/*
+ * Per-phase timing of the next calls: when `enable` is non-zero,
+ * safr_reconstruct records CUDA events around each of its kernels on its
+ * stream.  safr_trace_read synchronises on the last recorded event and
+ * writes up to `n` phase durations in milliseconds (pad+row FFT, column
+ * FFT+apply+inverse column FFT, inverse row FFT+resample+store) of the last
+ * traced call; returns the number of phases in *n_out.
+ */
+safr_status safr_trace(safr_plan_t plan, int enable);
+safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
+
+/* Number of kernel launches one safr_reconstruct makes for this plan. */
+int safr_launches_per_frame(safr_plan_t plan);
+
+/* Free every device and host resource of the plan (synchronises its device). */
+safr_status safr_destroy(safr_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char *safr_status_string(safr_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SAFR_H */

@@ -1,0 +1,123 @@
+// Internal plan of the SAFR library: host-side geometry and the device
+// buffers that one plan owns.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+#include <vector>
+
+#include "safr.h"
+
+namespace safr {
+
+// One star group of the split tomography (Section 3.3): all LGS stars, or all
+// NGS stars.
+struct Group {
+    int kind = SAFR_NGS;
+    int G = 0;
+    std::vector<int> stars;  // star indices in geometry order
+    std::vector<double> c;   // [L] cone coefficient c_l (Section 2)
+    std::vector<double> sx;  // [G][L] alpha_g^x h_l / (c_l delta): shift in layer pixels
+    std::vector<double> sy;  // [G][L]
+    double alpha = 0;        // Tikhonov parameter of the group
+    int b_row0 = 0;          // first B row of this group inside a column block
+    bool resample = false;   // layers move from pitch c_l*delta to delta (metric output)
+};
+
+// Geometry of one group handed to the precompute kernel (device pointers).
+struct PreGroupDev {
+    int G, L, b_row0;
+    double alpha;
+    const double *sx, *sy;  // [G][L]
+    const double *sw;       // [L] gamma_l^{1/2} / c_l
+    const double *tau;      // [L] pi^2 / (c_l T)^2
+};
+
+// Per-group data the frame kernels need.
+struct GroupDev {
+    int G;
+    int b_row0;
+    int resample;
+    int star[SAFR_MAX_GROUP_G];
+};
+
+// Everything the three frame kernels read, passed by value.
+template <typename R>
+struct FrameParams {
+    using C = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
+    int M, P, L, G, Mh, o, ngroups, sumLG;
+    int lchunk;       // layers per inverse-FFT chunk in the column pass
+    int rows_per_cta; // output rows per CTA in the inverse row pass
+    int src_pairs;    // row pairs of smem per group in the inverse row pass
+    R delta;
+    R inv_M2;         // 1 / M^2 of IDFT2
+    const void *in;
+    const float *in_scales;
+    void *out;
+    float *out_scales;
+    const C *B;       // [Mh][sumLG][M]
+    C *w1;            // [G][P][Mh]     row spectra of the padded wavefronts
+    C *w2;            // [ngroups][L][M][Mh]  layer spectra after the inverse column pass
+    float *energy;    // [ngroups][L][Mh] Parseval partial sums (FP16 storage only)
+    const C *tw;      // [M] exp(-2 pi i t / M) from host FP64
+    const int *rs_i0; // [L][M] floor(M/2 + (p - M/2)/c_l), unwrapped (LGS group)
+    const R *rs_w;    // [L][M] fractional part
+    const unsigned char *mask; // [P][P] pupil mask (removeTT)
+    R tt_rows[2][3];  // rows 1 and 2 of the inverse 3x3 plane-fit normal matrix
+    int star_tt[SAFR_MAX_G];   // 1: remove this star's tip/tilt
+    GroupDev grp[2];
+    int *status;
+};
+
+}  // namespace safr
+
+struct safr_plan_s {
+    int device = 0;
+    int M = 0, P = 0, L = 0, G = 0, Mh = 0, o = 0;
+    int precision = SAFR_FP32, output_metric = 0, mixed = 0, remove_tt = 0;
+    double delta = 0, T = 0, beta = 0;
+    std::vector<double> h, gamma;
+    int ngroups = 0;
+    safr::Group grp[2];
+    int sumLG = 0;
+    int warnings = 0;
+    int precomputed = 0;
+    double tt_rows[2][3] = {{0}};
+    std::vector<int> star_tt;
+
+    // launch shapes chosen at plan creation
+    int lchunk = 1, rows_per_cta = 8, src_pairs = 4;
+    size_t smem_k1 = 0, smem_k2 = 0, smem_k3 = 0;
+    int k1_rows = 8;
+
+    // device memory owned by the plan
+    void *d_B = nullptr;
+    size_t b_bytes = 0;
+    void *d_w1 = nullptr, *d_w2 = nullptr;
+    float *d_energy = nullptr;
+    size_t ws_bytes = 0;
+    void *d_tw = nullptr;
+    int *d_rs_i0 = nullptr;
+    void *d_rs_w = nullptr;
+    unsigned char *d_mask = nullptr;
+    double *d_pre = nullptr;  // shifts, sw, tau of both groups (precompute)
+    int *d_status = nullptr;
+    void *d_in_stage = nullptr, *d_out_stage = nullptr;
+    float *d_in_scales_stage = nullptr, *d_out_scales_stage = nullptr;
+    size_t in_bytes = 0, out_bytes = 0;
+
+    // tracing
+    int trace = 0;
+    int traced = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace safr {
+// Launchers (reconstruct.cu, precompute.cu).
+cudaError_t launch_precompute(safr_plan_s *plan, cudaStream_t stream);
+cudaError_t launch_frame(safr_plan_s *plan, const void *in, const float *in_scales, void *out,
+                         float *out_scales, cudaStream_t stream);
+cudaError_t configure_frame_kernels(safr_plan_s *plan);
+int launches_per_frame(const safr_plan_s *plan);
+}  // namespace safr

@@ -1,0 +1,263 @@
+"""Python binding of the SAFR C ABI (include/safr.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA
+kernels of libsafr.so.  The functions keep the C names; device buffers are
+torch CUDA tensors (or raw integer device pointers), streams are torch
+streams (or raw cudaStream_t integers).  There is no fallback: if the library
+cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SAFR_OK = 0
+SAFR_ERR_INVALID_ARG = 1
+SAFR_ERR_UNSUPPORTED_SIZE = 2
+SAFR_ERR_MISALIGNED = 3
+SAFR_ERR_NOT_PRECOMPUTED = 4
+SAFR_ERR_OOM = 5
+SAFR_ERR_CUDA = 6
+SAFR_ERR_TIMEOUT = 7
+SAFR_ERR_DEVICE = 8
+
+SAFR_NGS, SAFR_LGS = 0, 1
+SAFR_FP32, SAFR_FP16_STORAGE, SAFR_FP64 = 0, 1, 2
+SAFR_NATIVE, SAFR_METRIC = 0, 1
+SAFR_WARN_CONTAINMENT = 1
+
+_PRECISION = {"fp32": SAFR_FP32, "fp16": SAFR_FP16_STORAGE, "fp64": SAFR_FP64}
+_EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_reconstruct_host",
+            "safr_get_status", "safr_get_plan_info", "safr_copy_B", "safr_trace", "safr_trace_read",
+            "safr_launches_per_frame", "safr_destroy", "safr_status_string"]
+
+
+class SafrError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {safr_status_string(status)}")
+
+
+class safr_geometry(C.Structure):
+    _fields_ = [("M", C.c_int), ("P", C.c_int), ("pitch_m", C.c_double), ("diameter_m", C.c_double),
+                ("obstruction", C.c_double), ("L", C.c_int), ("h_m", C.POINTER(C.c_double)),
+                ("cn2", C.POINTER(C.c_double)), ("G", C.c_int), ("dir_x", C.POINTER(C.c_double)),
+                ("dir_y", C.POINTER(C.c_double)), ("kind", C.POINTER(C.c_int)), ("h_lgs_m", C.c_double),
+                ("alpha", C.c_double), ("alpha_tt", C.c_double), ("beta", C.c_double),
+                ("precision", C.c_int), ("output_grid", C.c_int), ("remove_tt", C.c_int)]
+
+
+class safr_plan_info(C.Structure):
+    _fields_ = [("M", C.c_int), ("P", C.c_int), ("L", C.c_int), ("G", C.c_int), ("ngroups", C.c_int),
+                ("group_kind", C.c_int * 2), ("group_G", C.c_int * 2), ("b_bytes", C.c_size_t),
+                ("workspace_bytes", C.c_size_t), ("in_bytes", C.c_size_t), ("out_bytes", C.c_size_t),
+                ("warnings", C.c_int), ("precomputed", C.c_int)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsafr.so (building it first if needed and possible)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build_library()
+    if not os.path.exists(path):
+        raise OSError(f"libsafr.so is not built ({path}); run paper_2510_19542_gb300/build.py")
+    lib = C.CDLL(path)
+    vp = C.c_void_p
+    lib.safr_plan_create.argtypes = [C.POINTER(safr_geometry), C.c_int, C.POINTER(vp)]
+    lib.safr_precompute.argtypes = [vp, vp]
+    lib.safr_reconstruct.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.safr_reconstruct_host.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.safr_get_status.argtypes = [vp]
+    lib.safr_get_plan_info.argtypes = [vp, C.POINTER(safr_plan_info)]
+    lib.safr_copy_B.argtypes = [vp, C.c_int, vp]
+    lib.safr_trace.argtypes = [vp, C.c_int]
+    lib.safr_trace_read.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
+    lib.safr_launches_per_frame.argtypes = [vp]
+    lib.safr_destroy.argtypes = [vp]
+    lib.safr_status_string.argtypes = [C.c_int]
+    lib.safr_status_string.restype = C.c_char_p
+    for name in _EXPORTS:
+        if name not in ("safr_status_string",):
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != SAFR_OK:
+        raise SafrError(status, where)
+
+
+def _ptr(x):
+    """Device or host pointer of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            return torch.cuda.current_stream().cuda_stream
+        except Exception:  # noqa: BLE001 - no torch / no CUDA: the legacy default stream
+            return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def safr_status_string(status: int) -> str:
+    return load().safr_status_string(int(status)).decode()
+
+
+def make_geometry(geom: dict):
+    """safr_geometry from a dict (keys of synth.config); returns (struct, keepalive)."""
+    h = np.ascontiguousarray(geom["h"], np.float64)
+    cn2 = np.ascontiguousarray(geom["cn2"], np.float64)
+    dx = np.ascontiguousarray(geom["dir_x"], np.float64)
+    dy = np.ascontiguousarray(geom["dir_y"], np.float64)
+    kind = np.ascontiguousarray(geom["kind"], np.int32)
+    prec = geom.get("precision", "fp32")
+    prec = _PRECISION[prec] if isinstance(prec, str) else int(prec)
+    dp = C.POINTER(C.c_double)
+    g = safr_geometry(
+        M=int(geom["M"]), P=int(geom["P"]), pitch_m=float(geom["pitch"]),
+        diameter_m=float(geom.get("diameter", 0.0)), obstruction=float(geom.get("obstruction", 0.0)),
+        L=len(h), h_m=h.ctypes.data_as(dp), cn2=cn2.ctypes.data_as(dp), G=len(dx),
+        dir_x=dx.ctypes.data_as(dp), dir_y=dy.ctypes.data_as(dp),
+        kind=kind.ctypes.data_as(C.POINTER(C.c_int)), h_lgs_m=float(geom.get("h_lgs", 90e3)),
+        alpha=float(geom["alpha"]), alpha_tt=float(geom.get("alpha_tt", geom["alpha"])),
+        beta=float(geom["beta"]), precision=prec,
+        output_grid=SAFR_METRIC if int(geom.get("output_metric", 1)) else SAFR_NATIVE,
+        remove_tt=int(geom.get("remove_tt", 1)))
+    return g, (h, cn2, dx, dy, kind)
+
+
+def safr_plan_create(geom: dict, cuda_device: int = 0) -> int:
+    g, keep = make_geometry(geom)
+    out = C.c_void_p()
+    _check(load().safr_plan_create(C.byref(g), int(cuda_device), C.byref(out)), "safr_plan_create")
+    del keep
+    return out.value
+
+
+def safr_precompute(plan: int, stream=None):
+    _check(load().safr_precompute(plan, _stream(stream)), "safr_precompute")
+
+
+def safr_reconstruct(plan: int, wavefronts, layers, in_scales=None, out_scales=None, stream=None):
+    _check(load().safr_reconstruct(plan, _ptr(wavefronts), _ptr(in_scales), _ptr(layers), _ptr(out_scales),
+                                   _stream(stream)), "safr_reconstruct")
+
+
+def safr_reconstruct_host(plan: int, wavefronts, layers, in_scales=None, out_scales=None, stream=None):
+    _check(load().safr_reconstruct_host(plan, _ptr(wavefronts), _ptr(in_scales), _ptr(layers),
+                                        _ptr(out_scales), _stream(stream)), "safr_reconstruct_host")
+
+
+def safr_get_status(plan: int) -> int:
+    return load().safr_get_status(plan)
+
+
+def safr_get_plan_info(plan: int) -> dict:
+    info = safr_plan_info()
+    _check(load().safr_get_plan_info(plan, C.byref(info)), "safr_get_plan_info")
+    return {k: (list(getattr(info, k)) if k in ("group_kind", "group_G") else getattr(info, k))
+            for k, _ in safr_plan_info._fields_}
+
+
+def safr_copy_B(plan: int, group: int) -> np.ndarray:
+    """B of one group as complex128 [M/2][L][G_group][M] (k, l, g, j)."""
+    info = safr_get_plan_info(plan)
+    M, L, Gg = info["M"], info["L"], info["group_G"][group]
+    out = np.empty((M // 2, L, Gg, M, 2), np.float64)
+    _check(load().safr_copy_B(plan, int(group), out.ctypes.data), "safr_copy_B")
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def safr_trace(plan: int, enable: bool = True):
+    _check(load().safr_trace(plan, int(bool(enable))), "safr_trace")
+
+
+def safr_trace_read(plan: int):
+    ms = (C.c_float * 8)()
+    n = C.c_int(0)
+    _check(load().safr_trace_read(plan, ms, 8, C.byref(n)), "safr_trace_read")
+    return [ms[i] for i in range(n.value)]
+
+
+def safr_launches_per_frame(plan: int) -> int:
+    return load().safr_launches_per_frame(plan)
+
+
+def safr_destroy(plan: int):
+    _check(load().safr_destroy(plan), "safr_destroy")
+
+
+class Plan:
+    """Owning wrapper: create, precompute, reconstruct with torch tensors."""
+
+    def __init__(self, geom: dict, device: int = 0, precompute: bool = True, stream=None):
+        self.geom = dict(geom)
+        self.handle = safr_plan_create(geom, device)
+        self.device = device
+        self.info = safr_get_plan_info(self.handle)
+        if precompute:
+            safr_precompute(self.handle, stream)
+            self.info["precomputed"] = 1
+
+    def close(self):
+        if getattr(self, "handle", None):
+            safr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    @property
+    def io_dtype(self):
+        import torch
+        return {"fp32": torch.float32, "fp16": torch.float16, "fp64": torch.float64}[
+            self.geom.get("precision", "fp32")]
+
+    def empty_layers(self):
+        import torch
+        return torch.empty((self.info["L"], self.info["M"], self.info["M"]), dtype=self.io_dtype,
+                           device=f"cuda:{self.device}")
+
+    def reconstruct(self, wavefronts, layers=None, in_scales=None, out_scales=None, stream=None):
+        import torch
+        if layers is None:
+            layers = self.empty_layers()
+        if self.geom.get("precision") == "fp16" and out_scales is None:
+            out_scales = torch.empty(self.info["L"], dtype=torch.float32, device=layers.device)
+        safr_reconstruct(self.handle, wavefronts, layers, in_scales, out_scales, stream)
+        return (layers, out_scales) if out_scales is not None else layers

@@ -1,0 +1,94 @@
+"""The C ABI library: builds, loads, exports every declared entry point, and
+rejects invalid arguments on the host before touching the GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "safr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(safr_[a-z_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2510_19542_gb300 import safr
+    return safr.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = _declared_functions()
+    assert len(names) >= 10, names
+    for n in names:
+        assert hasattr(lib, n), f"libsafr.so does not export {n}"
+
+
+def test_binding_names_match_the_abi():
+    from paper_2510_19542_gb300 import safr
+    for n in _declared_functions():
+        assert callable(getattr(safr, n, None)), f"binding lacks {n}"
+
+
+def test_status_strings(lib):
+    from paper_2510_19542_gb300 import safr
+    for s in range(9):
+        assert safr.safr_status_string(s).startswith("SAFR_")
+    assert "unknown" in safr.safr_status_string(99)
+
+
+def _geom(**kw):
+    from paper_2510_19542_gb300 import synth
+    g = synth.scaled(synth.config(2), M=64, P=20)
+    g.update(kw)
+    return g
+
+
+@pytest.mark.parametrize("change,status", [
+    (dict(M=48), 2),                       # not a power of two
+    (dict(M=2048, P=20), 2),               # above the maximum grid
+    (dict(P=65), 1),                       # pupil larger than the grid
+    (dict(pitch=0.0), 1),
+    (dict(alpha=0.0), 1),
+    (dict(beta=-1.0), 1),
+    (dict(h=np.array([0.0, 8000, 4000, 9000, 10000, 11000, 12000, 13000, 14000])), 1),  # not ascending
+    (dict(h=np.linspace(0, 95000.0, 9)), 1),  # above the sodium layer
+    (dict(cn2=np.zeros(9)), 1),
+    (dict(output_metric=0), 1),            # mixed plan needs the metric grid
+    (dict(alpha_tt=0.0), 1),
+    (dict(kind=np.array([0, 1, 2, 0, 0, 0, 0, 0, 0], np.int32)), 1),
+    (dict(precision=7), 1),
+])
+def test_plan_create_rejects_bad_geometry(lib, change, status):
+    from paper_2510_19542_gb300 import safr
+    g = _geom(**change)
+    with pytest.raises(safr.SafrError) as ei:
+        safr.safr_plan_create(g, 0)
+    assert ei.value.status == status
+
+
+def test_null_arguments(lib):
+    from paper_2510_19542_gb300 import safr
+    assert lib.safr_plan_create(None, 0, None) == safr.SAFR_ERR_INVALID_ARG
+    out = C.c_void_p()
+    assert lib.safr_plan_create(None, 0, C.byref(out)) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_precompute(None, None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_reconstruct(None, None, None, None, None, None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_destroy(None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_launches_per_frame(None) == 0
+
+
+def test_plan_create_without_gpu_reports_cuda_error(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2510_19542_gb300 import safr
+    with pytest.raises(safr.SafrError) as ei:
+        safr.safr_plan_create(_geom(), 0)
+    assert ei.value.status == safr.SAFR_ERR_CUDA

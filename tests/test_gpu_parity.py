@@ -1,0 +1,242 @@
+"""GPU path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerances: relative L2 error <= 1e-5 for FP32, <= 1e-3 for FP16 storage,
+<= 1e-12 for the FP64 instantiation, overall and per layer (per-layer errors
+are taken relative to the RMS of the whole output, because the weak high
+layers carry errors set by the strong ones).  B from the GPU precompute (a
+Cholesky solve) is compared with the oracle's (a Jacobi SVD) at 1e-12 in FP64.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def safr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr as s
+    s.load()
+    return s
+
+
+@pytest.fixture(scope="module")
+def synth():
+    from paper_2510_19542_gb300 import synth as s
+    return s
+
+
+TOL = {"fp32": 1e-5, "fp16": 1e-3, "fp64": 1e-12}
+DT = {"fp32": np.float32, "fp16": np.float16, "fp64": np.float64}
+
+
+def rel_errors(got, ref):
+    diff = got - ref
+    overall = np.linalg.norm(diff) / np.linalg.norm(ref)
+    scale = np.sqrt(np.mean(ref ** 2))
+    per_layer = np.sqrt(np.mean(diff ** 2, axis=(1, 2))) / scale
+    own = np.sqrt(np.mean(diff ** 2, axis=(1, 2))) / np.sqrt(np.mean(ref ** 2, axis=(1, 2)))
+    return overall, per_layer, own
+
+
+def run_gpu(safr, geom, x, in_scales=None):
+    prec = geom.get("precision", "fp32")
+    plan = safr.Plan(geom, device=0)
+    xin = torch.from_numpy(np.ascontiguousarray(x.astype(DT[prec]))).cuda()
+    sc = torch.from_numpy(in_scales).cuda() if in_scales is not None else None
+    out = plan.reconstruct(xin, in_scales=sc)
+    torch.cuda.synchronize()
+    assert safr.safr_get_status(plan.handle) == 0
+    if isinstance(out, tuple):
+        layers, scales = out
+        got = layers.double().cpu().numpy() * scales.double().cpu().numpy()[:, None, None]
+    else:
+        got = out.double().cpu().numpy()
+    return plan, got
+
+
+def check(safr, oracle_mod, geom, x, tol=None, in_scales=None, x_oracle=None):
+    prec = geom.get("precision", "fp32")
+    tol = TOL[prec] if tol is None else tol
+    ref = oracle_mod.OraclePlan(geom).reconstruct(x if x_oracle is None else x_oracle)
+    plan, got = run_gpu(safr, geom, x, in_scales)
+    plan.close()
+    overall, per_layer, own = rel_errors(got, ref)
+    assert overall <= tol, (overall, per_layer)
+    assert np.all(per_layer <= tol), per_layer
+    return overall, per_layer, own
+
+
+# ----------------------------------------------------------------------------
+# B: GPU Cholesky route vs oracle Jacobi-SVD route
+# ----------------------------------------------------------------------------
+@pytest.mark.parametrize("k,M,P,L", [(1, 32, 32, None), (2, 64, 20, None), (3, 64, 64, 35), (2, 32, 10, 4)])
+def test_precompute_B_matches_oracle(safr, synth, oracle_mod, k, M, P, L):
+    geom = synth.scaled(synth.config(k), M=M, P=P, L=L)
+    geom["precision"] = "fp64"
+    pl = safr.Plan(geom, device=0)
+    orc = oracle_mod.OraclePlan(geom)
+    for gi in range(pl.info["ngroups"]):
+        Bg = safr.safr_copy_B(pl.handle, gi)              # [k][l][g][j]
+        _, stars, _, Bo = orc.group(gi)                   # [j][k][l][g]
+        Bo = np.transpose(Bo[:, :M // 2], (1, 2, 3, 0))
+        err = np.abs(Bg - Bo).max() / np.abs(Bo).max()
+        assert err <= 1e-12, (gi, err)
+        assert np.all(Bg[:, :, :, M // 2] == 0)           # Nyquist row
+    pl.close()
+
+
+def test_precompute_B_fp32_rounding(safr, synth, oracle_mod):
+    geom = synth.scaled(synth.config(2), M=64, P=20)
+    pl = safr.Plan(geom, device=0)
+    orc = oracle_mod.OraclePlan(geom)
+    for gi in range(2):
+        Bg = safr.safr_copy_B(pl.handle, gi)
+        Bo = np.transpose(orc.group(gi)[3][:, :32], (1, 2, 3, 0))
+        assert np.abs(Bg - Bo).max() <= 1e-6 * np.abs(Bo).max()
+    pl.close()
+
+
+# ----------------------------------------------------------------------------
+# Whole frames
+# ----------------------------------------------------------------------------
+def test_tiny_ngs_fp64(safr, synth, oracle_mod):
+    g = synth.config(1)
+    check(safr, oracle_mod, g, synth.frame(g))
+
+
+def test_tiny_ngs_fp32(safr, synth, oracle_mod):
+    g = dict(synth.config(1), precision="fp32")
+    check(safr, oracle_mod, g, synth.frame(g))
+
+
+@pytest.mark.parametrize("M,P,L", [(64, 20, None), (128, 40, None), (64, 37, 5), (32, 9, 3), (8, 8, 2),
+                                   (16, 5, 9), (256, 80, 12)])
+def test_mixed_lgs_ngs_fp32(safr, synth, oracle_mod, M, P, L):
+    """Split tomography with removeTT and the metric resample; odd P gives a
+    ragged last row pair and an odd pad offset."""
+    g = synth.scaled(synth.config(2), M=M, P=P, L=L)
+    check(safr, oracle_mod, g, synth.frame(g))
+
+
+def test_mixed_lgs_ngs_fp64(safr, synth, oracle_mod):
+    g = dict(synth.scaled(synth.config(2), M=64, P=21), precision="fp64")
+    check(safr, oracle_mod, g, synth.frame(g))
+
+
+def test_lgs_only_native_and_metric(safr, synth, oracle_mod):
+    base = synth.scaled(synth.config(2), M=64, P=20)
+    lgs = [i for i in range(9) if base["kind"][i] == 1]
+    for metric in (0, 1):
+        g = dict(base, dir_x=base["dir_x"][lgs], dir_y=base["dir_y"][lgs], kind=base["kind"][lgs],
+                 output_metric=metric)
+        check(safr, oracle_mod, g, synth.frame(g))
+
+
+def test_many_layers_chunked(safr, synth, oracle_mod):
+    """L = 35 on a 512 grid: the column pass runs the inverse FFTs in layer chunks."""
+    g = dict(synth.scaled(synth.config(3), M=512, P=160, L=35), precision="fp32")
+    x = synth.random_frame(g, 5)
+    check(safr, oracle_mod, g, x)
+
+
+def test_fp16_storage(safr, synth, oracle_mod):
+    g = synth.scaled(synth.config(3), M=64, P=64, L=35)
+    x = synth.frame(g)
+    h, sc = synth.to_fp16_storage(x)
+    check(safr, oracle_mod, g, h, in_scales=sc, x_oracle=synth.from_fp16_storage(h, sc))
+
+
+def test_degenerate_layers_and_single_star(safr, synth, oracle_mod):
+    rng = np.random.default_rng(0)
+    # every layer at the ground: A(n) has rank one at every n
+    g = dict(synth.scaled(synth.config(1), M=32, P=32), h=np.array([0.0, 1e-6, 2e-6]), precision="fp64")
+    check(safr, oracle_mod, g, rng.standard_normal((3, 32, 32)))
+    # one star, one layer, beta = 0
+    g = dict(synth.scaled(synth.config(1), M=16, P=12), h=np.array([5000.0]), cn2=np.array([1.0]),
+             dir_x=np.array([2e-4]), dir_y=np.array([-1e-4]), kind=np.zeros(1, np.int32), beta=0.0,
+             precision="fp64")
+    check(safr, oracle_mod, g, rng.standard_normal((1, 12, 12)))
+
+
+def test_asymmetric_asterism_no_transpose(safr, synth, oracle_mod):
+    rng = np.random.default_rng(4)
+    g = synth.scaled(synth.config(2), M=64, P=24)
+    g["dir_x"] = rng.uniform(-6e-4, 6e-4, 9)
+    g["dir_y"] = rng.uniform(-2e-4, 2e-4, 9)
+    check(safr, oracle_mod, g, synth.random_frame(g, 3))
+
+
+def test_full_size_morfeo_frame(safr, synth, oracle_mod):
+    """The benchmarked workload at full size: 256 grid, 80 pupil, 6 LGS + 3 NGS, 9 layers."""
+    g = synth.config(2)
+    check(safr, oracle_mod, g, synth.frame(g))
+
+
+def test_full_size_fp16_512_sampled(safr, synth, oracle_mod):
+    """512 grid, 35 layers, FP16 storage at full size, checked on sampled outputs."""
+    g = synth.config(3)
+    x = synth.random_frame(g, 11) * 5.0
+    h, sc = synth.to_fp16_storage(x)
+    plan, got = run_gpu(safr, g, h, sc)
+    plan.close()
+    rng = np.random.default_rng(1)
+    lpq = np.stack([rng.integers(0, 35, 96), rng.integers(0, 512, 96), rng.integers(0, 512, 96)], 1)
+    ref = oracle_mod.OraclePlan(g).reconstruct_samples(synth.from_fp16_storage(h, sc), lpq)
+    gs = got[lpq[:, 0], lpq[:, 1], lpq[:, 2]]
+    assert np.linalg.norm(gs - ref) / np.linalg.norm(ref) <= 1e-3
+
+
+# ----------------------------------------------------------------------------
+# Properties of the GPU path
+# ----------------------------------------------------------------------------
+def test_deterministic_and_host_entry(safr, synth):
+    g = synth.scaled(synth.config(2), M=64, P=20)
+    x = synth.frame(g).astype(np.float32)
+    plan = safr.Plan(g, device=0)
+    xin = torch.from_numpy(x).cuda()
+    a = plan.reconstruct(xin).cpu().numpy()
+    b = plan.reconstruct(xin).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    host_out = np.empty_like(a)
+    safr.safr_reconstruct_host(plan.handle, np.ascontiguousarray(x), host_out)
+    np.testing.assert_array_equal(host_out, a)
+    plan.close()
+
+
+def test_runtime_argument_errors(safr, synth):
+    g = synth.scaled(synth.config(2), M=32, P=10)
+    h = safr.safr_plan_create(g, 0)
+    x = torch.zeros((9, 10, 10), device="cuda")
+    out = torch.zeros((9, 32, 32), device="cuda")
+    with pytest.raises(safr.SafrError) as ei:
+        safr.safr_reconstruct(h, x, out)
+    assert ei.value.status == safr.SAFR_ERR_NOT_PRECOMPUTED
+    safr.safr_precompute(h)
+    with pytest.raises(safr.SafrError) as ei:
+        safr.safr_reconstruct(h, x.data_ptr() + 4, out)
+    assert ei.value.status == safr.SAFR_ERR_MISALIGNED
+    with pytest.raises(safr.SafrError) as ei:
+        safr.safr_reconstruct(h, x, out, out_scales=torch.zeros(9, device="cuda"))
+    assert ei.value.status == safr.SAFR_ERR_INVALID_ARG
+    safr.safr_reconstruct(h, x, out)
+    torch.cuda.synchronize()
+    assert float(out.abs().max()) == 0.0  # linear map of a zero frame
+    assert safr.safr_get_status(h) == 0
+    info = safr.safr_get_plan_info(h)
+    assert info["ngroups"] == 2 and info["group_G"] == [6, 3] and info["precomputed"] == 1
+    safr.safr_destroy(h)
+
+
+def test_trace_phases(safr, synth):
+    g = synth.config(2)
+    plan = safr.Plan(g, device=0)
+    x = torch.from_numpy(synth.random_frame(g, 1).astype(np.float32)).cuda()
+    safr.safr_trace(plan.handle, True)
+    plan.reconstruct(x)
+    ms = safr.safr_trace_read(plan.handle)
+    assert len(ms) == safr.safr_launches_per_frame(plan.handle) and all(m > 0 for m in ms)
+    plan.close()
