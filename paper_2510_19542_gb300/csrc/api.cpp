@@ -40,7 +40,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 void free_plan_memory(safr_plan_s *p)
 {
-    void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask,
+    void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask, p->d_tt_w,
                     p->d_pre, p->d_status, p->d_in_stage, p->d_out_stage, p->d_in_scales_stage,
                     p->d_out_scales_stage};
     for (void *b : bufs)
@@ -177,9 +177,12 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     }
     p->sumLG = row0;
 
-    // removeTT: inverse of the plane-fit normal matrix over the pupil mask
+    // removeTT: the tip b and tilt c of the least-squares plane a + b x + c y
+    // over the pupil mask are linear in psi: (a, b, c) = N^{-1} sum_mask (1, x, y) psi,
+    // N = sum_mask (1, x, y)^T (1, x, y).  The two weight images are formed here in FP64.
     p->star_tt.assign(g->G, 0);
     std::vector<unsigned char> mask((size_t)g->P * g->P, 1);
+    std::vector<double> ttw(2 * (size_t)g->P * g->P, 0.0);
     if (p->remove_tt) {
         const double ro = g->diameter_m / 2.0, ri = g->obstruction * g->diameter_m / 2.0;
         double N[3][3] = {{0}};
@@ -196,10 +199,15 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
             }
         double inv[3][3];
         if (!invert3(N, inv)) return SAFR_ERR_INVALID_ARG;
-        for (int c = 0; c < 3; ++c) {
-            p->tt_rows[0][c] = inv[1][c];
-            p->tt_rows[1][c] = inv[2][c];
-        }
+        const size_t PP = (size_t)g->P * g->P;
+        for (int a = 0; a < g->P; ++a)
+            for (int b = 0; b < g->P; ++b) {
+                const size_t i = (size_t)a * g->P + b;
+                if (!mask[i]) continue;
+                const double x = (a - (g->P - 1) / 2.0) * g->pitch_m, y = (b - (g->P - 1) / 2.0) * g->pitch_m;
+                ttw[i] = inv[1][0] + inv[1][1] * x + inv[1][2] * y;
+                ttw[PP + i] = inv[2][0] + inv[2][1] * x + inv[2][2] * y;
+            }
         for (int i = 0; i < g->G; ++i) p->star_tt[i] = g->kind[i] == SAFR_LGS;
     }
 
@@ -258,6 +266,12 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
         SAFR_TRY(upload((float **)&p->d_rs_w, ff));
     }
     SAFR_TRY(upload(&p->d_mask, mask));
+    if (p->precision == SAFR_FP64) {
+        SAFR_TRY(upload((double **)&p->d_tt_w, ttw));
+    } else {
+        std::vector<float> tf(ttw.begin(), ttw.end());
+        SAFR_TRY(upload((float **)&p->d_tt_w, tf));
+    }
 
     // precompute inputs: per group sx, sy [G][L], sw [L], tau [L]
     std::vector<double> pre;

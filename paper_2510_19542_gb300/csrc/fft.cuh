@@ -80,14 +80,17 @@ __device__ __forceinline__ void dft_radix(C *v)
 // f * fstride in both buffers).  Ns is the length of the sub-transforms
 // already done (1 for the first pass).
 template <int RADIX, bool INV, typename C>
-__device__ __forceinline__ void stockham_pass(const C *__restrict__ src, C *__restrict__ dst, int M,
-                                              int Ns, int nfft, int fstride, const C *__restrict__ tw,
+__device__ __forceinline__ void stockham_pass(const C *__restrict__ src, C *__restrict__ dst, int logM,
+                                              int logNs, int nfft, int fstride, const C *__restrict__ tw,
                                               int tid, int nth)
 {
-    const int nb = M / RADIX;  // butterflies per sequence
-    const int tstep = M / (Ns * RADIX);
-    for (int idx = tid; idx < nfft * nb; idx += nth) {
-        const int f = idx / nb, j = idx - f * nb;
+    constexpr int LR = RADIX == 8 ? 3 : (RADIX == 4 ? 2 : 1);
+    const int lognb = logM - LR;           // butterflies per sequence: M / RADIX
+    const int nb = 1 << lognb;
+    const int Ns = 1 << logNs;
+    const int ltstep = logM - logNs - LR;  // twiddle stride M / (Ns RADIX)
+    for (int idx = tid; idx < (nfft << lognb); idx += nth) {
+        const int f = idx >> lognb, j = idx & (nb - 1);
         const C *s = src + f * fstride;
         C *d = dst + f * fstride;
         C v[RADIX];
@@ -97,12 +100,12 @@ __device__ __forceinline__ void stockham_pass(const C *__restrict__ src, C *__re
         if (Ns > 1) {
 #pragma unroll
             for (int r = 1; r < RADIX; ++r) {
-                C w = tw[r * k * tstep];
+                C w = tw[(r * k) << ltstep];
                 v[r] = cmul(v[r], INV ? cconj(w) : w);
             }
         }
         dft_radix<RADIX, INV>(v);
-        const int base = (j - k) * RADIX + k;
+        const int base = ((j - k) << LR) + k;
 #pragma unroll
         for (int r = 0; r < RADIX; ++r) d[base + r * Ns] = v[r];
     }
@@ -128,19 +131,20 @@ __host__ __device__ inline int fft_radix(int logM, int pass)
 // block must call it; it synchronises the block between passes and before
 // returning.
 template <bool INV, typename C>
-__device__ C *block_fft(C *a, C *b, int M, int logM, int nfft, int fstride, const C *tw, int tid, int nth)
+__device__ C *block_fft(C *a, C *b, int logM, int nfft, int fstride, const C *tw, int tid, int nth)
 {
-    int Ns = 1;
+    int logNs = 0;
     C *s = a, *d = b;
     const int np = fft_num_passes(logM);
     for (int pass = 0; pass < np; ++pass) {
-        const int R = fft_radix(logM, pass);
-        if (R == 8)
-            stockham_pass<8, INV>(s, d, M, Ns, nfft, fstride, tw, tid, nth);
-        else
-            stockham_pass<4, INV>(s, d, M, Ns, nfft, fstride, tw, tid, nth);
+        if (fft_radix(logM, pass) == 8) {
+            stockham_pass<8, INV>(s, d, logM, logNs, nfft, fstride, tw, tid, nth);
+            logNs += 3;
+        } else {
+            stockham_pass<4, INV>(s, d, logM, logNs, nfft, fstride, tw, tid, nth);
+            logNs += 2;
+        }
         __syncthreads();
-        Ns *= R;
         C *t = s;
         s = d;
         d = t;

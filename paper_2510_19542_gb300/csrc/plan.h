@@ -46,7 +46,7 @@ struct GroupDev {
 template <typename R>
 struct FrameParams {
     using C = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
-    int M, P, L, G, Mh, o, ngroups, sumLG;
+    int M, P, L, G, Mh, o, ngroups, sumLG, logM;
     int lchunk;       // layers per inverse-FFT chunk in the column pass
     int rows_per_cta; // output rows per CTA in the inverse row pass
     int src_pairs;    // row pairs of smem per group in the inverse row pass
@@ -64,7 +64,9 @@ struct FrameParams {
     const int *rs_i0; // [L][M] floor(M/2 + (p - M/2)/c_l), unwrapped (LGS group)
     const R *rs_w;    // [L][M] fractional part
     const unsigned char *mask; // [P][P] pupil mask (removeTT)
-    R tt_rows[2][3];  // rows 1 and 2 of the inverse 3x3 plane-fit normal matrix
+    const R *tt_w;    // [2][P][P] tip and tilt of the least-squares plane as linear functionals of psi
+    const char *prefetch;      // B, prefetched into L2 by the first pass
+    size_t prefetch_bytes;
     int star_tt[SAFR_MAX_G];   // 1: remove this star's tip/tilt
     GroupDev grp[2];
     int *status;
@@ -83,11 +85,12 @@ struct safr_plan_s {
     int sumLG = 0;
     int warnings = 0;
     int precomputed = 0;
-    double tt_rows[2][3] = {{0}};
     std::vector<int> star_tt;
 
     // launch shapes chosen at plan creation
     int lchunk = 1, rows_per_cta = 8, src_pairs = 4;
+    int pdl = 1;  // programmatic dependent launch between the three passes
+    int gmax = 16; // compile-time bound on stars per group of the column pass
     size_t smem_k1 = 0, smem_k2 = 0, smem_k3 = 0;
     int k1_rows = 8;
 
@@ -101,6 +104,7 @@ struct safr_plan_s {
     int *d_rs_i0 = nullptr;
     void *d_rs_w = nullptr;
     unsigned char *d_mask = nullptr;
+    void *d_tt_w = nullptr;
     double *d_pre = nullptr;  // shifts, sw, tau of both groups (precompute)
     int *d_status = nullptr;
     void *d_in_stage = nullptr, *d_out_stage = nullptr;

@@ -4,7 +4,8 @@
 //                     (Section 2), remove the LGS tip/tilt of a mixed plan
 //                     (Algorithm 3, line 3), real-to-complex FFT of the P
 //                     non-zero rows (two real rows per complex transform)
-//                     -> w1[g][p][k], k < M/2.
+//                     -> w1[g][p][k], k < M/2.  Its CTAs also start streaming
+//                     B from HBM into L2 for pass 2.
 //   pass 2 (columns): per column k and star group: FFT of the G columns
 //                     (P non-zero inputs each) -> d_g(j, k); per frequency
 //                     b_l = sum_g B_lg d_g for every layer (Algorithm 1,
@@ -15,6 +16,12 @@
 //                     layers from pitch c_l*delta to delta (metric output),
 //                     sum of the two groups (Algorithm 3, line 4), store.
 //
+// The passes are chained with programmatic dependent launch: each kernel
+// lets the next one launch at its start, and waits (griddepcontrol.wait, a
+// hardware wait with no spinning) for its predecessor before it reads or
+// writes any frame buffer.  Work before the wait touches only constant plan
+// data, so the launch latency of passes 2 and 3 is hidden.
+//
 // The Nyquist row and column of the even grid carry no B (B = 0 there), so
 // only k in [0, M/2) is kept between the passes.
 #include <cuda_fp16.h>
@@ -24,11 +31,21 @@
 #include <cmath>
 #include <cstring>
 #include <type_traits>
+#include <utility>
 
 #include "fft.cuh"
 #include "plan.h"
 
 namespace safr {
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ float to_real(T v);
@@ -65,9 +82,21 @@ __global__ void __launch_bounds__(256) k_rows_forward(FrameParams<R> fp)
 {
     using C = typename FrameParams<R>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int M = fp.M, P = fp.P, Mh = fp.Mh, o = fp.o;
-    int logM = 0;
-    while ((1 << logM) < M) ++logM;
+    pdl_trigger();
+    const int M = fp.M, P = fp.P, Mh = fp.Mh, o = fp.o, logM = fp.logM;
+    const int tid = threadIdx.x, nth = blockDim.x;
+
+    // stream this CTA's share of B into L2 for pass 2 (constant plan data)
+    if (fp.prefetch_bytes) {
+        const int nb = gridDim.x * gridDim.y;
+        const int b = blockIdx.y * gridDim.x + blockIdx.x;
+        const size_t share = ((fp.prefetch_bytes + nb - 1) / nb + 4095) & ~(size_t)4095;
+        const size_t lo = (size_t)b * share;
+        const size_t hi = min(fp.prefetch_bytes, lo + share);
+        for (size_t off = lo + (size_t)tid * 4096; off < hi; off += (size_t)nth * 4096)
+            prefetch_l2(fp.prefetch + off, (unsigned)min((size_t)4096, hi - off));
+    }
+
     const int g = blockIdx.y;
     const int rows = fp.rows_per_cta;  // even
     const int row0 = blockIdx.x * rows;
@@ -75,62 +104,59 @@ __global__ void __launch_bounds__(256) k_rows_forward(FrameParams<R> fp)
     const int nrows = min(rows, P - row0);
     const int npairs = (nrows + 1) >> 1;
     C *bufA = (C *)smem;
-    C *bufB = bufA + (size_t)npairs * M;
-    double *red = (double *)(bufB + (size_t)npairs * M);
+    C *bufB = bufA + ((size_t)npairs << logM);
+    R *red = (R *)(bufB + ((size_t)npairs << logM));
     C *tw = (C *)(red + 32);
-    const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < M; i += nth) tw[i] = fp.tw[i];
 
+    pdl_wait();
     const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
     const R scale = fp.in_scales ? (R)fp.in_scales[g] : R(1);
     const R half = R(0.5) * (R)(P - 1);
+    const bool tt = fp.star_tt[g] != 0;
 
-    // least-squares plane over the pupil mask: (a, b, c) = N^{-1} (sum psi, sum x psi, sum y psi)
+    // tip and tilt of the least-squares plane over the pupil mask: linear
+    // functionals sum_i w_b[i] psi[i], sum_i w_c[i] psi[i] (weights from the
+    // host FP64 inverse of the 3x3 normal matrix)
     R tb = 0, tc = 0;
-    if (fp.star_tt[g]) {
-        double m0 = 0, mx = 0, my = 0;
+    if (tt) {
+        const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
+        R sb = 0, sc = 0;
         for (int i = tid; i < P * P; i += nth) {
-            if (!fp.mask[i]) continue;
-            const int a = i / P, b = i - a * P;
-            const double v = (double)(load_in<R>(psi + i) * scale);
-            const double x = ((double)a - 0.5 * (P - 1)) * (double)fp.delta;
-            const double y = ((double)b - 0.5 * (P - 1)) * (double)fp.delta;
-            m0 += v;
-            mx += x * v;
-            my += y * v;
+            const R v = load_in<R>(psi + i);
+            sb += wb[i] * v;
+            sc += wc[i] * v;
         }
-        m0 = block_sum(m0, red);
-        mx = block_sum(mx, red);
-        my = block_sum(my, red);
-        tb = (R)(fp.tt_rows[0][0] * m0 + fp.tt_rows[0][1] * mx + fp.tt_rows[0][2] * my);
-        tc = (R)(fp.tt_rows[1][0] * m0 + fp.tt_rows[1][1] * mx + fp.tt_rows[1][2] * my);
+        tb = block_sum(sb, red) * scale;
+        tc = block_sum(sc, red) * scale;
     }
 
     // z[q] = psi[row 2i][q - o] + i psi[row 2i+1][q - o], zero outside the pupil
-    for (int idx = tid; idx < npairs * M; idx += nth) {
-        const int i = idx / M, q = idx - i * M;
+    for (int idx = tid; idx < (npairs << logM); idx += nth) {
+        const int i = idx >> logM, q = idx & (M - 1);
         const int qq = q - o;
         R re = 0, im = 0;
         if (qq >= 0 && qq < P) {
             const int a0 = row0 + 2 * i, a1 = a0 + 1;
             const R y = ((R)qq - half) * fp.delta;
             re = load_in<R>(psi + (size_t)a0 * P + qq) * scale;
-            if (fp.star_tt[g] && fp.mask[a0 * P + qq]) re -= tb * (((R)a0 - half) * fp.delta) + tc * y;
+            if (tt && fp.mask[a0 * P + qq]) re -= tb * (((R)a0 - half) * fp.delta) + tc * y;
             if (2 * i + 1 < nrows) {
                 im = load_in<R>(psi + (size_t)a1 * P + qq) * scale;
-                if (fp.star_tt[g] && fp.mask[a1 * P + qq]) im -= tb * (((R)a1 - half) * fp.delta) + tc * y;
+                if (tt && fp.mask[a1 * P + qq]) im -= tb * (((R)a1 - half) * fp.delta) + tc * y;
             }
         }
         bufA[idx] = C{re, im};
     }
     __syncthreads();
-    C *res = block_fft<false>(bufA, bufB, M, logM, npairs, M, tw, tid, nth);
+    C *res = block_fft<false>(bufA, bufB, logM, npairs, M, tw, tid, nth);
 
     // split the two real transforms: X1 = (Z[k] + conj Z[M-k]) / 2, X2 = (Z[k] - conj Z[M-k]) / 2i
-    for (int idx = tid; idx < npairs * Mh; idx += nth) {
-        const int i = idx / Mh, k = idx - i * Mh;
-        const C z = res[i * M + k];
-        const C zc = res[i * M + ((M - k) & (M - 1))];
+    const int logMh = logM - 1;
+    for (int idx = tid; idx < (npairs << logMh); idx += nth) {
+        const int i = idx >> logMh, k = idx & (Mh - 1);
+        const C z = res[(i << logM) + k];
+        const C zc = res[(i << logM) + ((M - k) & (M - 1))];
         const C x1 = C{R(0.5) * (z.x + zc.x), R(0.5) * (z.y - zc.y)};
         const C x2 = C{R(0.5) * (z.y + zc.y), R(0.5) * (zc.x - z.x)};
         const int a0 = row0 + 2 * i;
@@ -142,53 +168,66 @@ __global__ void __launch_bounds__(256) k_rows_forward(FrameParams<R> fp)
 // ----------------------------------------------------------------------------
 // pass 2: column FFT + per-frequency apply + inverse column FFT
 // ----------------------------------------------------------------------------
-template <typename R>
+template <typename R, int GMAX>
 __global__ void __launch_bounds__(256) k_cols_apply(FrameParams<R> fp)
 {
     using C = typename FrameParams<R>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int M = fp.M, P = fp.P, Mh = fp.Mh, o = fp.o, L = fp.L;
-    int logM = 0;
-    while ((1 << logM) < M) ++logM;
+    pdl_trigger();
+    const int M = fp.M, P = fp.P, Mh = fp.Mh, o = fp.o, L = fp.L, logM = fp.logM;
     const int k = blockIdx.x;
     const int gi = blockIdx.y;
     const GroupDev &gr = fp.grp[gi];
     const int Gg = gr.G;
     const int W = max(Gg, fp.lchunk);
-    C *dcol = (C *)smem;               // [Gg][M]
-    C *bufA = dcol + (size_t)Gg * M;   // [W][M]
-    C *bufB = bufA + (size_t)W * M;    // [W][M]
-    C *tw = bufB + (size_t)W * M;      // [M]
+    C *dcol = (C *)smem;                    // [Gg][M]
+    C *bufA = dcol + ((size_t)Gg << logM);  // [W][M]
+    C *bufB = bufA + ((size_t)W << logM);   // [W][M]
+    C *tw = bufB + ((size_t)W << logM);     // [M]
     R *red = (R *)(tw + M);
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < M; i += nth) tw[i] = fp.tw[i];
 
-    for (int idx = tid; idx < Gg * M; idx += nth) {
-        const int t = idx / M, p = idx - t * M;
+    pdl_wait();
+    for (int idx = tid; idx < (Gg << logM); idx += nth) {
+        const int t = idx >> logM, p = idx & (M - 1);
         const int pp = p - o;
         C v = C{0, 0};
         if (pp >= 0 && pp < P) v = fp.w1[((size_t)gr.star[t] * P + pp) * Mh + k];
-        bufA[idx] = v;
+        dcol[idx] = v;
     }
     __syncthreads();
-    C *res = block_fft<false>(bufA, bufB, M, logM, Gg, M, tw, tid, nth);
-    for (int idx = tid; idx < Gg * M; idx += nth) dcol[idx] = res[idx];
-    __syncthreads();
+    // forward column transforms, result copied back into dcol if it landed in bufA
+    C *res = block_fft<false>(dcol, bufA, logM, Gg, M, tw, tid, nth);
+    if (res != dcol) {
+        for (int idx = tid; idx < (Gg << logM); idx += nth) dcol[idx] = res[idx];
+        __syncthreads();
+    }
 
     const C *Bk = fp.B + ((size_t)k * fp.sumLG + gr.b_row0) * M;
     for (int l0 = 0; l0 < L; l0 += fp.lchunk) {
         const int lc = min(fp.lchunk, L - l0);
-        for (int idx = tid; idx < lc * M; idx += nth) {
-            const int l = idx / M, j = idx - l * M;
-            const C *Bl = Bk + (size_t)(l0 + l) * Gg * M + j;
-            R ar = 0, ai = 0;
-            for (int t = 0; t < Gg; ++t) {
-                const C b = Bl[(size_t)t * M];
-                const C d = dcol[t * M + j];
-                ar += b.x * d.x - b.y * d.y;
-                ai += b.x * d.y + b.y * d.x;
+        for (int j = tid; j < M; j += nth) {
+            C d[GMAX];
+#pragma unroll
+            for (int t = 0; t < GMAX; ++t)
+                if (t < Gg) d[t] = dcol[(t << logM) + j];
+            const C *Bj = Bk + (size_t)l0 * Gg * M + j;
+#pragma unroll 2
+            for (int l = 0; l < lc; ++l) {
+                C bv[GMAX];
+#pragma unroll
+                for (int t = 0; t < GMAX; ++t)
+                    if (t < Gg) bv[t] = __ldg(Bj + ((size_t)(l * Gg + t) << logM));
+                R ar = 0, ai = 0;
+#pragma unroll
+                for (int t = 0; t < GMAX; ++t)
+                    if (t < Gg) {
+                        ar += bv[t].x * d[t].x - bv[t].y * d[t].y;
+                        ai += bv[t].x * d[t].y + bv[t].y * d[t].x;
+                    }
+                bufA[(l << logM) + j] = C{ar, ai};
             }
-            bufA[idx] = C{ar, ai};
         }
         __syncthreads();
         if (fp.energy) {
@@ -197,16 +236,16 @@ __global__ void __launch_bounds__(256) k_cols_apply(FrameParams<R> fp)
             for (int l = 0; l < lc; ++l) {
                 R e = 0;
                 for (int j = tid; j < M; j += nth) {
-                    const C v = bufA[l * M + j];
+                    const C v = bufA[(l << logM) + j];
                     e += v.x * v.x + v.y * v.y;
                 }
                 e = block_sum(e, red);
                 if (tid == 0) fp.energy[((size_t)gi * L + l0 + l) * Mh + k] = (float)(k == 0 ? e : R(2) * e);
             }
         }
-        res = block_fft<true>(bufA, bufB, M, logM, lc, M, tw, tid, nth);
-        for (int idx = tid; idx < lc * M; idx += nth) {
-            const int l = idx / M, p = idx - l * M;
+        res = block_fft<true>(bufA, bufB, logM, lc, M, tw, tid, nth);
+        for (int idx = tid; idx < (lc << logM); idx += nth) {
+            const int l = idx >> logM, p = idx & (M - 1);
             fp.w2[(((size_t)gi * L + l0 + l) * M + p) * Mh + k] = res[idx];
         }
         __syncthreads();
@@ -224,29 +263,26 @@ template <>
 __device__ __forceinline__ void store_out<__half>(__half *p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ void store_out_d(double *p, double v) { *p = v; }
 
-__device__ __forceinline__ int wrap_index(int i, int M) { return ((i % M) + M) % M; }
-
 template <typename R, typename TOUT>
 __global__ void __launch_bounds__(256) k_rows_inverse(FrameParams<R> fp)
 {
     using C = typename FrameParams<R>::C;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int M = fp.M, Mh = fp.Mh, L = fp.L;
-    int logM = 0;
-    while ((1 << logM) < M) ++logM;
+    pdl_trigger();
+    const int M = fp.M, Mh = fp.Mh, L = fp.L, logM = fp.logM;
     const int l = blockIdx.y;
     const int p0 = blockIdx.x * fp.rows_per_cta;
     const int nr = min(fp.rows_per_cta, M - p0);
     const int SP = fp.src_pairs;
-    C *bufA = (C *)smem;                 // [SP][M]
-    C *bufB = bufA + (size_t)SP * M;     // [SP][M]
-    C *tw = bufB + (size_t)SP * M;       // [M]
-    R *acc = (R *)(tw + M);              // [rows][M]
+    C *bufA = (C *)smem;                    // [SP][M]
+    C *bufB = bufA + ((size_t)SP << logM);  // [SP][M]
+    C *tw = bufB + ((size_t)SP << logM);    // [M]
+    R *acc = (R *)(tw + M);                 // [rows][M]
     const int tid = threadIdx.x, nth = blockDim.x;
     for (int i = tid; i < M; i += nth) tw[i] = fp.tw[i];
-    for (int i = tid; i < nr * M; i += nth) acc[i] = 0;
-    __syncthreads();
+    for (int i = tid; i < (nr << logM); i += nth) acc[i] = 0;
 
+    pdl_wait();
     for (int gi = 0; gi < fp.ngroups; ++gi) {
         const bool rs = fp.grp[gi].resample;
         int first, nsrc;
@@ -264,11 +300,11 @@ __global__ void __launch_bounds__(256) k_rows_inverse(FrameParams<R> fp)
         }
         const C *src = fp.w2 + ((size_t)gi * L + l) * M * Mh;
         // Z[k] = X1[k] + i X2[k] over the full length M from the stored half (Hermitian rows)
-        for (int idx = tid; idx < npairs * M; idx += nth) {
-            const int i = idx / M, k = idx - i * M;
-            const int ra = wrap_index(first + 2 * i, M);
+        for (int idx = tid; idx < (npairs << logM); idx += nth) {
+            const int i = idx >> logM, k = idx & (M - 1);
+            const int ra = (first + 2 * i) & (M - 1);
             const bool hasb = 2 * i + 1 < nsrc;
-            const int rb = wrap_index(first + 2 * i + 1, M);
+            const int rb = (first + 2 * i + 1) & (M - 1);
             C z = C{0, 0};
             if (k < Mh) {
                 C x1 = src[(size_t)ra * Mh + k];
@@ -288,10 +324,10 @@ __global__ void __launch_bounds__(256) k_rows_inverse(FrameParams<R> fp)
             bufA[idx] = z;
         }
         __syncthreads();
-        const C *res = block_fft<true>(bufA, bufB, M, logM, npairs, M, tw, tid, nth);
+        const C *res = block_fft<true>(bufA, bufB, logM, npairs, M, tw, tid, nth);
         // source row s (local) = res[s/2].x or .y
-        for (int idx = tid; idx < nr * M; idx += nth) {
-            const int r = idx / M, q = idx - r * M;
+        for (int idx = tid; idx < (nr << logM); idx += nth) {
+            const int r = idx >> logM, q = idx & (M - 1);
             R v;
             if (rs) {
                 const int pr = p0 + r;
@@ -299,14 +335,14 @@ __global__ void __launch_bounds__(256) k_rows_inverse(FrameParams<R> fp)
                 const R fu = fp.rs_w[l * M + pr];
                 const int j0u = fp.rs_i0[l * M + q];
                 const R fv = fp.rs_w[l * M + q];
-                const int ja = wrap_index(j0u, M), jb = wrap_index(j0u + 1, M);
-                const C ra = res[(i0 >> 1) * M + ja], rb = res[(i0 >> 1) * M + jb];
-                const C sa = res[((i0 + 1) >> 1) * M + ja], sb = res[((i0 + 1) >> 1) * M + jb];
+                const int ja = j0u & (M - 1), jb = (j0u + 1) & (M - 1);
+                const C ra = res[((i0 >> 1) << logM) + ja], rb = res[((i0 >> 1) << logM) + jb];
+                const C sa = res[(((i0 + 1) >> 1) << logM) + ja], sb = res[(((i0 + 1) >> 1) << logM) + jb];
                 const R v00 = (i0 & 1) ? ra.y : ra.x, v01 = (i0 & 1) ? rb.y : rb.x;
                 const R v10 = ((i0 + 1) & 1) ? sa.y : sa.x, v11 = ((i0 + 1) & 1) ? sb.y : sb.x;
                 v = (R(1) - fu) * ((R(1) - fv) * v00 + fv * v01) + fu * ((R(1) - fv) * v10 + fv * v11);
             } else {
-                const C c = res[(r >> 1) * M + q];
+                const C c = res[((r >> 1) << logM) + q];
                 v = (r & 1) ? c.y : c.x;
             }
             acc[idx] += v;
@@ -329,7 +365,7 @@ __global__ void __launch_bounds__(256) k_rows_inverse(FrameParams<R> fp)
     }
     TOUT *out = (TOUT *)fp.out + ((size_t)l * M + p0) * M;
     const R f = fp.inv_M2 * inv_scale;
-    for (int idx = tid; idx < nr * M; idx += nth) {
+    for (int idx = tid; idx < (nr << logM); idx += nth) {
         if constexpr (std::is_same<TOUT, double>::value)
             store_out_d(out + idx, (double)(acc[idx] * f));
         else
@@ -358,6 +394,9 @@ static FrameParams<R> make_params(safr_plan_s *pl, const void *in, const float *
     fp.o = pl->o;
     fp.ngroups = pl->ngroups;
     fp.sumLG = pl->sumLG;
+    int lm = 0;
+    while ((1 << lm) < pl->M) ++lm;
+    fp.logM = lm;
     fp.lchunk = pl->lchunk;
     fp.rows_per_cta = pl->rows_per_cta;
     fp.src_pairs = pl->src_pairs;
@@ -375,8 +414,9 @@ static FrameParams<R> make_params(safr_plan_s *pl, const void *in, const float *
     fp.rs_i0 = pl->d_rs_i0;
     fp.rs_w = (const R *)pl->d_rs_w;
     fp.mask = pl->d_mask;
-    for (int r = 0; r < 2; ++r)
-        for (int c = 0; c < 3; ++c) fp.tt_rows[r][c] = (R)pl->tt_rows[r][c];
+    fp.tt_w = (const R *)pl->d_tt_w;
+    fp.prefetch = (const char *)pl->d_B;
+    fp.prefetch_bytes = pl->b_bytes;
     for (int g = 0; g < pl->G; ++g) fp.star_tt[g] = pl->star_tt[g];
     for (int gi = 0; gi < pl->ngroups; ++gi) {
         fp.grp[gi].G = pl->grp[gi].G;
@@ -389,6 +429,13 @@ static FrameParams<R> make_params(safr_plan_s *pl, const void *in, const float *
 }
 
 int launches_per_frame(const safr_plan_s *) { return 3; }
+
+// column-pass instance for the largest star group of the plan
+template <typename R>
+static void (*cols_kernel(int gmax))(FrameParams<R>)
+{
+    return gmax == 4 ? k_cols_apply<R, 4> : (gmax == 8 ? k_cols_apply<R, 8> : k_cols_apply<R, 16>);
+}
 
 template <typename K1, typename K2, typename K3>
 static cudaError_t set_smem(K1 k1, K2 k2, K3 k3, const safr_plan_s *pl)
@@ -410,7 +457,7 @@ cudaError_t configure_frame_kernels(safr_plan_s *pl)
 
     // pass 1: rows per CTA (even), two buffers of rows/2 transforms
     pl->k1_rows = 8;
-    pl->smem_k1 = 2 * (size_t)(pl->k1_rows / 2) * M * cs + 32 * sizeof(double) + (size_t)M * cs;
+    pl->smem_k1 = 2 * (size_t)(pl->k1_rows / 2) * M * cs + 32 * rs + (size_t)M * cs;
 
     // pass 2: layers per inverse chunk so that dcol + 2 * max(Gg, chunk) rows fit
     int lc = pl->L;
@@ -440,11 +487,29 @@ cudaError_t configure_frame_kernels(safr_plan_s *pl)
     pl->src_pairs = sp;
     pl->smem_k3 = (2 * (size_t)sp * M + M) * cs + (size_t)pl->rows_per_cta * M * rs;
 
+    pl->gmax = maxGg <= 4 ? 4 : (maxGg <= 8 ? 8 : 16);
     if (pl->precision == SAFR_FP64)
-        return set_smem(k_rows_forward<double, double>, k_cols_apply<double>, k_rows_inverse<double, double>, pl);
+        return set_smem(k_rows_forward<double, double>, cols_kernel<double>(pl->gmax), k_rows_inverse<double, double>, pl);
     if (pl->precision == SAFR_FP16_STORAGE)
-        return set_smem(k_rows_forward<float, __half>, k_cols_apply<float>, k_rows_inverse<float, __half>, pl);
-    return set_smem(k_rows_forward<float, float>, k_cols_apply<float>, k_rows_inverse<float, float>, pl);
+        return set_smem(k_rows_forward<float, __half>, cols_kernel<float>(pl->gmax), k_rows_inverse<float, __half>, pl);
+    return set_smem(k_rows_forward<float, float>, cols_kernel<float>(pl->gmax), k_rows_inverse<float, float>, pl);
+}
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch(void (*kernel)(KArgs...), dim3 grid, size_t smem, cudaStream_t st, bool pdl,
+                          Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <typename R, typename TIN, typename TOUT>
@@ -455,14 +520,21 @@ static cudaError_t run_frame(safr_plan_s *pl, const void *in, const float *in_sc
     const dim3 g1((pl->P + pl->k1_rows - 1) / pl->k1_rows, pl->G);
     const dim3 g2(pl->Mh, pl->ngroups);
     const dim3 g3((pl->M + pl->rows_per_cta - 1) / pl->rows_per_cta, pl->L);
+    // events between the passes would break the programmatic overlap, so a
+    // traced call runs the passes plainly serialised
+    const bool pdl = pl->pdl && !pl->trace;
+    cudaError_t e;
     if (pl->trace) cudaEventRecord(pl->ev[0], st);
     fp.rows_per_cta = pl->k1_rows;
-    k_rows_forward<R, TIN><<<g1, 256, pl->smem_k1, st>>>(fp);
+    e = launch(k_rows_forward<R, TIN>, g1, pl->smem_k1, st, pdl, fp);
+    if (e != cudaSuccess) return e;
     if (pl->trace) cudaEventRecord(pl->ev[1], st);
     fp.rows_per_cta = pl->rows_per_cta;
-    k_cols_apply<R><<<g2, 256, pl->smem_k2, st>>>(fp);
+    e = launch(cols_kernel<R>(pl->gmax), g2, pl->smem_k2, st, pdl, fp);
+    if (e != cudaSuccess) return e;
     if (pl->trace) cudaEventRecord(pl->ev[2], st);
-    k_rows_inverse<R, TOUT><<<g3, 256, pl->smem_k3, st>>>(fp);
+    e = launch(k_rows_inverse<R, TOUT>, g3, pl->smem_k3, st, pdl, fp);
+    if (e != cudaSuccess) return e;
     if (pl->trace) {
         cudaEventRecord(pl->ev[3], st);
         pl->traced = 1;
