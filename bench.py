@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--impl", default="safr", choices=["safr", "reference"])
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", default="auto", choices=["auto", "fused", "passes"])
     return ap.parse_args()
 
 
@@ -194,7 +195,7 @@ def run_safr(args):
                "sample": f"{n} full frames of the workload in {dt:.1f} s (FP64 oracle, naive DFT2; its "
                          "Jacobi-SVD B precompute untimed)"}
 
-    plan = safr.Plan(g, device=local)
+    plan = safr.Plan(g, device=local, path={"auto": 0, "fused": 1, "passes": 2}[args.path])
     stream = torch.cuda.current_stream(dev)
     frames = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in frames_np]
     layers = plan.empty_layers()
@@ -272,7 +273,7 @@ def run_safr(args):
         rel_l2 = float(np.linalg.norm(got - ref_layers[fi]) / np.linalg.norm(ref_layers[fi]))
 
     if rank == 0:
-        ph = np.array(phases)  # [steps][3]
+        ph = np.array(phases)  # [steps][launches]
         ph_mean = ph.mean(axis=0).tolist()
         M, Mh = info["M"], info["M"] // 2
         sumLG = info["L"] * info["G"]
@@ -288,12 +289,17 @@ def run_safr(args):
             pass
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-        k2_s = ph_mean[1] * 1e-3
-        achieved = b_bytes / k2_s / 1e9
+        if launches == 1:
+            kname, k_bytes, k_s = "k_frame", frame_bytes, ph_mean[0] * 1e-3
+            phase_names = ["frame"]
+        else:
+            kname, k_bytes, k_s = "k_cols_apply", b_bytes, ph_mean[1] * 1e-3
+            phase_names = ["rows_forward", "cols_apply", "rows_inverse"]
+        achieved = k_bytes / k_s / 1e9
         traffic = None
         try:
             with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-                traffic = json.load(f).get(WORKLOAD, {}).get("k_cols_apply")
+                traffic = json.load(f).get(WORKLOAD, {}).get(kname)
         except (OSError, ValueError):
             traffic = None
         lat_sorted = sorted(lat)
@@ -306,12 +312,12 @@ def run_safr(args):
             "latency_ms": {"p50": lat_sorted[len(lat) // 2],
                            "p99": lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                            "mean": total_ms / args.steps},
-            "phases_ms": {"rows_forward": ph_mean[0], "cols_apply": ph_mean[1], "rows_inverse": ph_mean[2]},
+            "kernels_ms": dict(zip(phase_names, ph_mean)), "path": "fused" if launches == 1 else "passes",
             "frame_roofline": {"bytes": frame_bytes, "achieved_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
                                "peak_gbs": hbm, "frac": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9 / hbm},
-            "roofline": {"kernel": "k_cols_apply", "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                         "algorithmic_bytes": b_bytes},
+                         "algorithmic_bytes": k_bytes},
             "clocks": clk, "gpu_launches": launches * args.steps, "device_status": status,
             "rel_l2_vs_oracle": rel_l2,
             "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": UNIT,

@@ -75,6 +75,13 @@ enum { SAFR_NATIVE = 0, SAFR_METRIC = 1 };                     /* output grid   
 #define SAFR_MAX_G 32       /* stars per plan                   */
 #define SAFR_MAX_GROUP_G 16 /* stars per group (LGS or NGS)     */
 
+/* Kernel schedules of safr_reconstruct (safr_set_path). */
+enum {
+    SAFR_PATH_AUTO = 0,  /* the persistent kernel when the plan fits it, else the three passes */
+    SAFR_PATH_FUSED = 1, /* one persistent cooperative kernel with two grid barriers          */
+    SAFR_PATH_PASSES = 2 /* three kernels chained by programmatic dependent launch           */
+};
+
 /* Warning bits of safr_plan_info.warnings. */
 #define SAFR_WARN_CONTAINMENT 1 /* c_l Omega_A + alpha_g h_l is not inside c_l Omega_T (Section 2) */
 
@@ -166,7 +173,10 @@ safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const f
 safr_status safr_reconstruct_host(safr_plan_t plan, const void *h_wavefronts, const float *h_in_scales,
                                   void *h_layers, float *h_out_scales, cudaStream_t stream);
 
-/* Sticky device-side status of the plan (synchronises the plan's device). */
+/*
+ * Sticky device-side status of the plan (synchronises the plan's device).
+ * Reading a non-OK status clears it and re-arms the plan's grid barrier.
+ */
 safr_status safr_get_status(safr_plan_t plan);
 
 /* Sizes, groups and warnings of a plan (host only, no synchronisation). */
@@ -185,15 +195,37 @@ safr_status safr_copy_B(safr_plan_t plan, int group, double *dst);
  * Per-phase timing of the next calls: when `enable` is non-zero,
  * safr_reconstruct records CUDA events around each of its kernels on its
  * stream.  safr_trace_read synchronises on the last recorded event and
- * writes up to `n` phase durations in milliseconds (pad+row FFT, column
- * FFT+apply+inverse column FFT, inverse row FFT+resample+store) of the last
- * traced call; returns the number of phases in *n_out.
+ * writes up to `n` kernel durations in milliseconds of the last traced call:
+ * one for SAFR_PATH_FUSED (the whole frame), three for SAFR_PATH_PASSES
+ * (pad+row FFT, column FFT+apply+inverse column FFT, inverse row
+ * FFT+resample+store; traced calls run them without programmatic overlap);
+ * returns the number of durations in *n_out.
  */
 safr_status safr_trace(safr_plan_t plan, int enable);
 safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
 
 /* Number of kernel launches one safr_reconstruct makes for this plan. */
 int safr_launches_per_frame(safr_plan_t plan);
+
+/*
+ * Choose the kernel schedule of the next calls (SAFR_PATH_*).  Both schedules
+ * compute the same layers.  SAFR_PATH_FUSED on a plan the persistent kernel
+ * cannot hold returns SAFR_ERR_UNSUPPORTED_SIZE and leaves the choice as it
+ * was.  safr_get_path returns the schedule that safr_reconstruct will use
+ * (SAFR_PATH_FUSED or SAFR_PATH_PASSES), or -1 for a NULL plan.
+ */
+safr_status safr_set_path(safr_plan_t plan, int path);
+int safr_get_path(safr_plan_t plan);
+
+/*
+ * Test hook for the bounded grid barrier of SAFR_PATH_FUSED: with cta >= 0,
+ * that CTA leaves the next frames before the first barrier, so every other
+ * CTA's wait runs out after timeout_s seconds and the kernel records
+ * SAFR_ERR_TIMEOUT (read by safr_get_status) instead of hanging.  cta = -1
+ * restores normal operation; timeout_s <= 0 restores the default limit (1 s).
+ * The frames computed meanwhile are invalid.
+ */
+safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s);
 
 /* Free every device and host resource of the plan (synchronises its device). */
 safr_status safr_destroy(safr_plan_t plan);

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -41,6 +42,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 void free_plan_memory(safr_plan_s *p)
 {
     void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask, p->d_tt_w,
+                    p->d_xy_hat, p->d_pm, p->d_bar,
                     p->d_pre, p->d_status, p->d_in_stage, p->d_out_stage, p->d_in_scales_stage,
                     p->d_out_scales_stage};
     for (void *b : bufs)
@@ -66,6 +68,46 @@ bool invert3(const double a[3][3], double inv[3][3])
     inv[2][1] = (a[0][1] * a[2][0] - a[0][0] * a[2][1]) / det;
     inv[2][2] = (a[0][0] * a[1][1] - a[0][1] * a[1][0]) / det;
     return true;
+}
+
+// In-place radix-2 FFT of length n (power of two), FP64, forward sign.
+void host_fft(std::vector<std::complex<double>> &a)
+{
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        for (size_t i = 0; i < n; i += len)
+            for (size_t k = 0; k < len / 2; ++k) {
+                const double ang = -2.0 * kPi * (double)k / (double)len;
+                const std::complex<double> w(std::cos(ang), std::sin(ang));
+                const std::complex<double> u = a[i + k], v = a[i + k + len / 2] * w;
+                a[i + k] = u + v;
+                a[i + k + len / 2] = u - v;
+            }
+    }
+}
+
+// DFT2 (Section 3.2) of an M x M real image, returned for k < M/2 as [k][j].
+std::vector<std::complex<double>> host_dft2_half(const std::vector<double> &img, int M)
+{
+    std::vector<std::complex<double>> rows((size_t)M * M), line(M);
+    for (int p = 0; p < M; ++p) {
+        for (int q = 0; q < M; ++q) line[q] = img[(size_t)p * M + q];
+        host_fft(line);
+        for (int k = 0; k < M; ++k) rows[(size_t)p * M + k] = line[k];
+    }
+    std::vector<std::complex<double>> out((size_t)(M / 2) * M);
+    for (int k = 0; k < M / 2; ++k) {
+        for (int p = 0; p < M; ++p) line[p] = rows[(size_t)p * M + k];
+        host_fft(line);
+        for (int j = 0; j < M; ++j) out[(size_t)k * M + j] = line[j];
+    }
+    return out;
 }
 
 safr_status validate(const safr_geometry *g)
@@ -272,6 +314,47 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
         std::vector<float> tf(ttw.begin(), ttw.end());
         SAFR_TRY(upload((float **)&p->d_tt_w, tf));
     }
+    // spectra of x and y on the pupil mask, placed in the padded grid, for the
+    // frequency-domain removeTT of the persistent kernel: DFT2(psi - b x - c y)
+    // = DFT2(psi) - b X - c Y
+    {
+        std::vector<double> xm((size_t)M * M, 0.0), ym((size_t)M * M, 0.0);
+        if (p->remove_tt)
+            for (int a = 0; a < g->P; ++a)
+                for (int bq = 0; bq < g->P; ++bq) {
+                    if (!mask[(size_t)a * g->P + bq]) continue;
+                    xm[(size_t)(a + p->o) * M + bq + p->o] = (a - (g->P - 1) / 2.0) * g->pitch_m;
+                    ym[(size_t)(a + p->o) * M + bq + p->o] = (bq - (g->P - 1) / 2.0) * g->pitch_m;
+                }
+        const size_t half = (size_t)Mh * M;
+        std::vector<std::complex<double>> xs, ys;
+        if (p->remove_tt) {
+            xs = host_dft2_half(xm, M);
+            ys = host_dft2_half(ym, M);
+        } else {
+            xs.assign(half, 0.0);
+            ys.assign(half, 0.0);
+        }
+        if (p->precision == SAFR_FP64) {
+            std::vector<double2> h(2 * half);
+            for (size_t i = 0; i < half; ++i) {
+                h[i] = make_double2(xs[i].real(), xs[i].imag());
+                h[half + i] = make_double2(ys[i].real(), ys[i].imag());
+            }
+            SAFR_TRY(upload((double2 **)&p->d_xy_hat, h));
+        } else {
+            std::vector<float2> h(2 * half);
+            for (size_t i = 0; i < half; ++i) {
+                h[i] = make_float2((float)xs[i].real(), (float)xs[i].imag());
+                h[half + i] = make_float2((float)ys[i].real(), (float)ys[i].imag());
+            }
+            SAFR_TRY(upload((float2 **)&p->d_xy_hat, h));
+        }
+    }
+    SAFR_TRY(cudaMalloc(&p->d_pm, (size_t)p->G * p->P * 2 * rs));
+    SAFR_TRY(cudaMemset(p->d_pm, 0, (size_t)p->G * p->P * 2 * rs));
+    SAFR_TRY(cudaMalloc((void **)&p->d_bar, 2 * sizeof(unsigned)));
+    SAFR_TRY(cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned)));
 
     // precompute inputs: per group sx, sy [G][L], sw [L], tau [L]
     std::vector<double> pre;
@@ -300,9 +383,17 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     if (e != cudaSuccess) return SAFR_ERR_CUDA;
     if (p->smem_k1 > 227 * 1024 || p->smem_k2 > 227 * 1024 || p->smem_k3 > 227 * 1024)
         return SAFR_ERR_UNSUPPORTED_SIZE;
-    (void)rs;
+    p->fused_ok = safr::configure_fused(p) ? 1 : 0;
+    cudaGetLastError();
 #undef SAFR_TRY
     return SAFR_OK;
+}
+
+cudaError_t dispatch(safr_plan_s *p, const void *in, const float *in_scales, void *out, float *out_scales,
+                     cudaStream_t st)
+{
+    if (safr::use_fused(p)) return safr::launch_fused(p, in, in_scales, out, out_scales, st);
+    return safr::launch_frame(p, in, in_scales, out, out_scales, st);
 }
 
 }  // namespace
@@ -358,8 +449,7 @@ safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const f
         return SAFR_ERR_MISALIGNED;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
-    if (safr::launch_frame(plan, d_wavefronts, d_in_scales, d_layers, d_out_scales, stream) != cudaSuccess)
-        return SAFR_ERR_CUDA;
+    if (dispatch(plan, d_wavefronts, d_in_scales, d_layers, d_out_scales, stream) != cudaSuccess) return SAFR_ERR_CUDA;
     return SAFR_OK;
 }
 
@@ -379,8 +469,8 @@ safr_status safr_reconstruct_host(safr_plan_t plan, const void *h_wavefronts, co
     if (h_in_scales && cudaMemcpyAsync(plan->d_in_scales_stage, h_in_scales, nsc_in, cudaMemcpyHostToDevice,
                                        stream) != cudaSuccess)
         return SAFR_ERR_CUDA;
-    if (safr::launch_frame(plan, plan->d_in_stage, h_in_scales ? plan->d_in_scales_stage : nullptr,
-                           plan->d_out_stage, fp16 ? plan->d_out_scales_stage : nullptr, stream) != cudaSuccess)
+    if (dispatch(plan, plan->d_in_stage, h_in_scales ? plan->d_in_scales_stage : nullptr, plan->d_out_stage,
+                 fp16 ? plan->d_out_scales_stage : nullptr, stream) != cudaSuccess)
         return SAFR_ERR_CUDA;
     if (cudaMemcpyAsync(h_layers, plan->d_out_stage, plan->out_bytes, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
         return SAFR_ERR_CUDA;
@@ -399,6 +489,12 @@ safr_status safr_get_status(safr_plan_t plan)
     if (cudaDeviceSynchronize() != cudaSuccess) return SAFR_ERR_CUDA;
     int st = 0;
     if (cudaMemcpy(&st, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SAFR_ERR_CUDA;
+    if (st != 0) {
+        // clear the sticky word and re-arm the grid barrier that a timeout left half-counted
+        if (cudaMemset(plan->d_status, 0, sizeof(int)) != cudaSuccess) return SAFR_ERR_CUDA;
+        if (cudaMemset(plan->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) return SAFR_ERR_CUDA;
+        if (cudaDeviceSynchronize() != cudaSuccess) return SAFR_ERR_CUDA;
+    }
     return (safr_status)st;
 }
 
@@ -477,8 +573,8 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out)
     if (!plan->traced) return SAFR_ERR_INVALID_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
-    if (cudaEventSynchronize(plan->ev[3]) != cudaSuccess) return SAFR_ERR_CUDA;
-    const int nph = 3;
+    const int nph = safr::launches_per_frame(plan);
+    if (cudaEventSynchronize(plan->ev[nph]) != cudaSuccess) return SAFR_ERR_CUDA;
     for (int i = 0; i < nph && i < n; ++i)
         if (cudaEventElapsedTime(&ms[i], plan->ev[i], plan->ev[i + 1]) != cudaSuccess) return SAFR_ERR_CUDA;
     if (n_out) *n_out = nph;
@@ -486,6 +582,29 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out)
 }
 
 int safr_launches_per_frame(safr_plan_t plan) { return plan ? safr::launches_per_frame(plan) : 0; }
+
+safr_status safr_set_path(safr_plan_t plan, int path)
+{
+    if (!plan || path < SAFR_PATH_AUTO || path > SAFR_PATH_PASSES) return SAFR_ERR_INVALID_ARG;
+    if (path == SAFR_PATH_FUSED && !plan->fused_ok) return SAFR_ERR_UNSUPPORTED_SIZE;
+    plan->path = path;
+    plan->traced = 0;
+    return SAFR_OK;
+}
+
+int safr_get_path(safr_plan_t plan)
+{
+    if (!plan) return -1;
+    return safr::use_fused(plan) ? SAFR_PATH_FUSED : SAFR_PATH_PASSES;
+}
+
+safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s)
+{
+    if (!plan || cta < -1) return SAFR_ERR_INVALID_ARG;
+    plan->debug_skip_cta = cta;
+    plan->barrier_timeout_ns = timeout_s > 0 ? (unsigned long long)(timeout_s * 1e9) : 1000000000ull;
+    return SAFR_OK;
+}
 
 safr_status safr_destroy(safr_plan_t plan)
 {

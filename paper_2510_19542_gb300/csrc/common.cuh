@@ -1,0 +1,53 @@
+// Device helpers shared by the frame kernels.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace safr {
+
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ float to_real(T v);
+template <>
+__device__ __forceinline__ float to_real<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_real<__half>(__half v) { return __half2float(v); }
+
+template <typename R, typename T>
+__device__ __forceinline__ R load_in(const T *p) { return (R)to_real<T>(*p); }
+template <>
+__device__ __forceinline__ double load_in<double, double>(const double *p) { return *p; }
+
+template <typename R>
+__device__ __forceinline__ R block_sum(R v, R *red)
+{
+    // deterministic: fixed shuffle tree, then fixed order over warps
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    R t = 0;
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    return t;
+}
+
+template <typename TOUT>
+__device__ __forceinline__ void store_out(TOUT *p, float v);
+template <>
+__device__ __forceinline__ void store_out<float>(float *p, float v) { *p = v; }
+template <>
+__device__ __forceinline__ void store_out<__half>(__half *p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ void store_out_d(double *p, double v) { *p = v; }
+
+}  // namespace safr

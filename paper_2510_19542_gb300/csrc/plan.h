@@ -90,6 +90,13 @@ struct safr_plan_s {
     // launch shapes chosen at plan creation
     int lchunk = 1, rows_per_cta = 8, src_pairs = 4;
     int pdl = 1;  // programmatic dependent launch between the three passes
+    int path = SAFR_PATH_AUTO;  // requested kernel schedule
+    int fused_ok = 0;           // the persistent kernel fits this plan
+    // persistent-kernel shapes
+    int f_grid = 0, f_npr = 0, f_n1 = 0, f_lchunk = 1, f_rt3 = 2, f_stage3 = 2, f_sp3 = 1, f_tiles3 = 1, f_n3 = 1;
+    size_t f_smem = 0;
+    int debug_skip_cta = -1;
+    unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
     int gmax = 16; // compile-time bound on stars per group of the column pass
     size_t smem_k1 = 0, smem_k2 = 0, smem_k3 = 0;
     int k1_rows = 8;
@@ -105,6 +112,9 @@ struct safr_plan_s {
     void *d_rs_w = nullptr;
     unsigned char *d_mask = nullptr;
     void *d_tt_w = nullptr;
+    void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT)
+    void *d_pm = nullptr;      // [G][P][2] per-row tip/tilt functionals
+    unsigned *d_bar = nullptr; // grid barrier words
     double *d_pre = nullptr;  // shifts, sw, tau of both groups (precompute)
     int *d_status = nullptr;
     void *d_in_stage = nullptr, *d_out_stage = nullptr;
@@ -124,4 +134,11 @@ cudaError_t launch_frame(safr_plan_s *plan, const void *in, const float *in_scal
                          float *out_scales, cudaStream_t stream);
 cudaError_t configure_frame_kernels(safr_plan_s *plan);
 int launches_per_frame(const safr_plan_s *plan);
+bool configure_fused(safr_plan_s *plan);
+cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scales, void *out, float *out_scales,
+                         cudaStream_t stream);
+inline bool use_fused(const safr_plan_s *plan)
+{
+    return plan->fused_ok && plan->path != SAFR_PATH_PASSES;
+}
 }  // namespace safr

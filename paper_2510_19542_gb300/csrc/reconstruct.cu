@@ -33,46 +33,11 @@
 #include <type_traits>
 #include <utility>
 
+#include "common.cuh"
 #include "fft.cuh"
 #include "plan.h"
 
 namespace safr {
-
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
-// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
-__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-template <typename T>
-__device__ __forceinline__ float to_real(T v);
-template <>
-__device__ __forceinline__ float to_real<float>(float v) { return v; }
-template <>
-__device__ __forceinline__ float to_real<__half>(__half v) { return __half2float(v); }
-
-template <typename R, typename T>
-__device__ __forceinline__ R load_in(const T *p) { return (R)to_real<T>(*p); }
-template <>
-__device__ __forceinline__ double load_in<double, double>(const double *p) { return *p; }
-
-template <typename R>
-__device__ __forceinline__ R block_sum(R v, R *red)
-{
-    // deterministic: fixed shuffle tree, then fixed order over warps
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) red[w] = v;
-    __syncthreads();
-    R t = 0;
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i) t += red[i];
-    return t;
-}
 
 // ----------------------------------------------------------------------------
 // pass 1: pad + removeTT + row FFT
@@ -255,14 +220,6 @@ __global__ void __launch_bounds__(256) k_cols_apply(FrameParams<R> fp)
 // ----------------------------------------------------------------------------
 // pass 3: inverse row FFT (complex to real) + resample + group sum + store
 // ----------------------------------------------------------------------------
-template <typename TOUT>
-__device__ __forceinline__ void store_out(TOUT *p, float v);
-template <>
-__device__ __forceinline__ void store_out<float>(float *p, float v) { *p = v; }
-template <>
-__device__ __forceinline__ void store_out<__half>(__half *p, float v) { *p = __float2half_rn(v); }
-__device__ __forceinline__ void store_out_d(double *p, double v) { *p = v; }
-
 template <typename R, typename TOUT>
 __global__ void __launch_bounds__(256) k_rows_inverse(FrameParams<R> fp)
 {
@@ -428,7 +385,7 @@ static FrameParams<R> make_params(safr_plan_s *pl, const void *in, const float *
     return fp;
 }
 
-int launches_per_frame(const safr_plan_s *) { return 3; }
+int launches_per_frame(const safr_plan_s *pl) { return use_fused(pl) ? 1 : 3; }
 
 // column-pass instance for the largest star group of the plan
 template <typename R>

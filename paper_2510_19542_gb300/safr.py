@@ -29,11 +29,13 @@ SAFR_NGS, SAFR_LGS = 0, 1
 SAFR_FP32, SAFR_FP16_STORAGE, SAFR_FP64 = 0, 1, 2
 SAFR_NATIVE, SAFR_METRIC = 0, 1
 SAFR_WARN_CONTAINMENT = 1
+SAFR_PATH_AUTO, SAFR_PATH_FUSED, SAFR_PATH_PASSES = 0, 1, 2
 
 _PRECISION = {"fp32": SAFR_FP32, "fp16": SAFR_FP16_STORAGE, "fp64": SAFR_FP64}
 _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_reconstruct_host",
             "safr_get_status", "safr_get_plan_info", "safr_copy_B", "safr_trace", "safr_trace_read",
-            "safr_launches_per_frame", "safr_destroy", "safr_status_string"]
+            "safr_launches_per_frame", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
+            "safr_destroy", "safr_status_string"]
 
 
 class SafrError(RuntimeError):
@@ -87,6 +89,9 @@ def load(build_if_missing: bool = True):
     lib.safr_trace.argtypes = [vp, C.c_int]
     lib.safr_trace_read.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     lib.safr_launches_per_frame.argtypes = [vp]
+    lib.safr_set_path.argtypes = [vp, C.c_int]
+    lib.safr_get_path.argtypes = [vp]
+    lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
     lib.safr_destroy.argtypes = [vp]
     lib.safr_status_string.argtypes = [C.c_int]
     lib.safr_status_string.restype = C.c_char_p
@@ -215,6 +220,18 @@ def safr_launches_per_frame(plan: int) -> int:
     return load().safr_launches_per_frame(plan)
 
 
+def safr_set_path(plan: int, path: int):
+    _check(load().safr_set_path(plan, int(path)), "safr_set_path")
+
+
+def safr_get_path(plan: int) -> int:
+    return load().safr_get_path(plan)
+
+
+def safr_debug_skip_barrier(plan: int, cta: int, timeout_s: float = 0.0):
+    _check(load().safr_debug_skip_barrier(plan, int(cta), float(timeout_s)), "safr_debug_skip_barrier")
+
+
 def safr_destroy(plan: int):
     _check(load().safr_destroy(plan), "safr_destroy")
 
@@ -222,11 +239,13 @@ def safr_destroy(plan: int):
 class Plan:
     """Owning wrapper: create, precompute, reconstruct with torch tensors."""
 
-    def __init__(self, geom: dict, device: int = 0, precompute: bool = True, stream=None):
+    def __init__(self, geom: dict, device: int = 0, precompute: bool = True, stream=None, path: int | None = None):
         self.geom = dict(geom)
         self.handle = safr_plan_create(geom, device)
         self.device = device
         self.info = safr_get_plan_info(self.handle)
+        if path is not None:
+            safr_set_path(self.handle, path)
         if precompute:
             safr_precompute(self.handle, stream)
             self.info["precomputed"] = 1

@@ -42,9 +42,19 @@ def rel_errors(got, ref):
     return overall, per_layer, own
 
 
-def run_gpu(safr, geom, x, in_scales=None):
+PATHS = {"fused": 1, "passes": 2}
+
+
+@pytest.fixture(params=["fused", "passes"])
+def path(request):
+    return PATHS[request.param]
+
+
+def run_gpu(safr, geom, x, in_scales=None, path=None):
     prec = geom.get("precision", "fp32")
-    plan = safr.Plan(geom, device=0)
+    plan = safr.Plan(geom, device=0, path=path)
+    if path is not None:
+        assert safr.safr_get_path(plan.handle) == path
     xin = torch.from_numpy(np.ascontiguousarray(x.astype(DT[prec]))).cuda()
     sc = torch.from_numpy(in_scales).cuda() if in_scales is not None else None
     out = plan.reconstruct(xin, in_scales=sc)
@@ -58,11 +68,11 @@ def run_gpu(safr, geom, x, in_scales=None):
     return plan, got
 
 
-def check(safr, oracle_mod, geom, x, tol=None, in_scales=None, x_oracle=None):
+def check(safr, oracle_mod, geom, x, tol=None, in_scales=None, x_oracle=None, path=None):
     prec = geom.get("precision", "fp32")
     tol = TOL[prec] if tol is None else tol
     ref = oracle_mod.OraclePlan(geom).reconstruct(x if x_oracle is None else x_oracle)
-    plan, got = run_gpu(safr, geom, x, in_scales)
+    plan, got = run_gpu(safr, geom, x, in_scales, path)
     plan.close()
     overall, per_layer, own = rel_errors(got, ref)
     assert overall <= tol, (overall, per_layer)
@@ -103,85 +113,85 @@ def test_precompute_B_fp32_rounding(safr, synth, oracle_mod):
 # ----------------------------------------------------------------------------
 # Whole frames
 # ----------------------------------------------------------------------------
-def test_tiny_ngs_fp64(safr, synth, oracle_mod):
+def test_tiny_ngs_fp64(safr, synth, oracle_mod, path):
     g = synth.config(1)
-    check(safr, oracle_mod, g, synth.frame(g))
+    check(safr, oracle_mod, g, synth.frame(g), path=path)
 
 
-def test_tiny_ngs_fp32(safr, synth, oracle_mod):
+def test_tiny_ngs_fp32(safr, synth, oracle_mod, path):
     g = dict(synth.config(1), precision="fp32")
-    check(safr, oracle_mod, g, synth.frame(g))
+    check(safr, oracle_mod, g, synth.frame(g), path=path)
 
 
 @pytest.mark.parametrize("M,P,L", [(64, 20, None), (128, 40, None), (64, 37, 5), (32, 9, 3), (8, 8, 2),
                                    (16, 5, 9), (256, 80, 12)])
-def test_mixed_lgs_ngs_fp32(safr, synth, oracle_mod, M, P, L):
+def test_mixed_lgs_ngs_fp32(safr, synth, oracle_mod, M, P, L, path):
     """Split tomography with removeTT and the metric resample; odd P gives a
     ragged last row pair and an odd pad offset."""
     g = synth.scaled(synth.config(2), M=M, P=P, L=L)
-    check(safr, oracle_mod, g, synth.frame(g))
+    check(safr, oracle_mod, g, synth.frame(g), path=path)
 
 
-def test_mixed_lgs_ngs_fp64(safr, synth, oracle_mod):
+def test_mixed_lgs_ngs_fp64(safr, synth, oracle_mod, path):
     g = dict(synth.scaled(synth.config(2), M=64, P=21), precision="fp64")
-    check(safr, oracle_mod, g, synth.frame(g))
+    check(safr, oracle_mod, g, synth.frame(g), path=path)
 
 
-def test_lgs_only_native_and_metric(safr, synth, oracle_mod):
+def test_lgs_only_native_and_metric(safr, synth, oracle_mod, path):
     base = synth.scaled(synth.config(2), M=64, P=20)
     lgs = [i for i in range(9) if base["kind"][i] == 1]
     for metric in (0, 1):
         g = dict(base, dir_x=base["dir_x"][lgs], dir_y=base["dir_y"][lgs], kind=base["kind"][lgs],
                  output_metric=metric)
-        check(safr, oracle_mod, g, synth.frame(g))
+        check(safr, oracle_mod, g, synth.frame(g), path=path)
 
 
-def test_many_layers_chunked(safr, synth, oracle_mod):
+def test_many_layers_chunked(safr, synth, oracle_mod, path):
     """L = 35 on a 512 grid: the column pass runs the inverse FFTs in layer chunks."""
     g = dict(synth.scaled(synth.config(3), M=512, P=160, L=35), precision="fp32")
     x = synth.random_frame(g, 5)
-    check(safr, oracle_mod, g, x)
+    check(safr, oracle_mod, g, x, path=path)
 
 
-def test_fp16_storage(safr, synth, oracle_mod):
+def test_fp16_storage(safr, synth, oracle_mod, path):
     g = synth.scaled(synth.config(3), M=64, P=64, L=35)
     x = synth.frame(g)
     h, sc = synth.to_fp16_storage(x)
-    check(safr, oracle_mod, g, h, in_scales=sc, x_oracle=synth.from_fp16_storage(h, sc))
+    check(safr, oracle_mod, g, h, in_scales=sc, x_oracle=synth.from_fp16_storage(h, sc), path=path)
 
 
-def test_degenerate_layers_and_single_star(safr, synth, oracle_mod):
+def test_degenerate_layers_and_single_star(safr, synth, oracle_mod, path):
     rng = np.random.default_rng(0)
     # every layer at the ground: A(n) has rank one at every n
     g = dict(synth.scaled(synth.config(1), M=32, P=32), h=np.array([0.0, 1e-6, 2e-6]), precision="fp64")
-    check(safr, oracle_mod, g, rng.standard_normal((3, 32, 32)))
+    check(safr, oracle_mod, g, rng.standard_normal((3, 32, 32)), path=path)
     # one star, one layer, beta = 0
     g = dict(synth.scaled(synth.config(1), M=16, P=12), h=np.array([5000.0]), cn2=np.array([1.0]),
              dir_x=np.array([2e-4]), dir_y=np.array([-1e-4]), kind=np.zeros(1, np.int32), beta=0.0,
              precision="fp64")
-    check(safr, oracle_mod, g, rng.standard_normal((1, 12, 12)))
+    check(safr, oracle_mod, g, rng.standard_normal((1, 12, 12)), path=path)
 
 
-def test_asymmetric_asterism_no_transpose(safr, synth, oracle_mod):
+def test_asymmetric_asterism_no_transpose(safr, synth, oracle_mod, path):
     rng = np.random.default_rng(4)
     g = synth.scaled(synth.config(2), M=64, P=24)
     g["dir_x"] = rng.uniform(-6e-4, 6e-4, 9)
     g["dir_y"] = rng.uniform(-2e-4, 2e-4, 9)
-    check(safr, oracle_mod, g, synth.random_frame(g, 3))
+    check(safr, oracle_mod, g, synth.random_frame(g, 3), path=path)
 
 
-def test_full_size_morfeo_frame(safr, synth, oracle_mod):
+def test_full_size_morfeo_frame(safr, synth, oracle_mod, path):
     """The benchmarked workload at full size: 256 grid, 80 pupil, 6 LGS + 3 NGS, 9 layers."""
     g = synth.config(2)
-    check(safr, oracle_mod, g, synth.frame(g))
+    check(safr, oracle_mod, g, synth.frame(g), path=path)
 
 
-def test_full_size_fp16_512_sampled(safr, synth, oracle_mod):
+def test_full_size_fp16_512_sampled(safr, synth, oracle_mod, path):
     """512 grid, 35 layers, FP16 storage at full size, checked on sampled outputs."""
     g = synth.config(3)
     x = synth.random_frame(g, 11) * 5.0
     h, sc = synth.to_fp16_storage(x)
-    plan, got = run_gpu(safr, g, h, sc)
+    plan, got = run_gpu(safr, g, h, sc, path)
     plan.close()
     rng = np.random.default_rng(1)
     lpq = np.stack([rng.integers(0, 35, 96), rng.integers(0, 512, 96), rng.integers(0, 512, 96)], 1)
@@ -193,10 +203,10 @@ def test_full_size_fp16_512_sampled(safr, synth, oracle_mod):
 # ----------------------------------------------------------------------------
 # Properties of the GPU path
 # ----------------------------------------------------------------------------
-def test_deterministic_and_host_entry(safr, synth):
+def test_deterministic_and_host_entry(safr, synth, path):
     g = synth.scaled(synth.config(2), M=64, P=20)
     x = synth.frame(g).astype(np.float32)
-    plan = safr.Plan(g, device=0)
+    plan = safr.Plan(g, device=0, path=path)
     xin = torch.from_numpy(x).cuda()
     a = plan.reconstruct(xin).cpu().numpy()
     b = plan.reconstruct(xin).cpu().numpy()
@@ -231,12 +241,46 @@ def test_runtime_argument_errors(safr, synth):
     safr.safr_destroy(h)
 
 
-def test_trace_phases(safr, synth):
+def test_trace_phases(safr, synth, path):
     g = synth.config(2)
-    plan = safr.Plan(g, device=0)
+    plan = safr.Plan(g, device=0, path=path)
     x = torch.from_numpy(synth.random_frame(g, 1).astype(np.float32)).cuda()
     safr.safr_trace(plan.handle, True)
     plan.reconstruct(x)
     ms = safr.safr_trace_read(plan.handle)
     assert len(ms) == safr.safr_launches_per_frame(plan.handle) and all(m > 0 for m in ms)
+    plan.close()
+
+
+def test_paths_agree(safr, synth):
+    """Both schedules on the full-size workload: same layers to FP32 rounding."""
+    g = synth.config(2)
+    x = torch.from_numpy(synth.frame(g).astype(np.float32)).cuda()
+    a = safr.Plan(g, device=0, path=1)
+    b = safr.Plan(g, device=0, path=2)
+    ya = a.reconstruct(x).double().cpu().numpy()
+    yb = b.reconstruct(x).double().cpu().numpy()
+    assert np.linalg.norm(ya - yb) / np.linalg.norm(yb) < 2e-6
+    a.close()
+    b.close()
+
+
+def test_grid_barrier_timeout_is_reported_not_hung(safr, synth):
+    """One CTA leaves before the first grid barrier: the others' bounded waits run
+    out, the kernel records SAFR_ERR_TIMEOUT, and the plan keeps working after
+    the status is read."""
+    g = synth.scaled(synth.config(2), M=64, P=20)
+    plan = safr.Plan(g, device=0, path=1)
+    x = torch.from_numpy(synth.frame(g).astype(np.float32)).cuda()
+    good = plan.reconstruct(x).clone()
+    safr.safr_debug_skip_barrier(plan.handle, 0, 0.02)
+    plan.reconstruct(x)
+    torch.cuda.synchronize()
+    assert safr.safr_get_status(plan.handle) == safr.SAFR_ERR_TIMEOUT
+    assert safr.safr_get_status(plan.handle) == 0  # cleared, barrier re-armed
+    safr.safr_debug_skip_barrier(plan.handle, -1, 0.0)
+    again = plan.reconstruct(x)
+    torch.cuda.synchronize()
+    assert safr.safr_get_status(plan.handle) == 0
+    assert torch.equal(again, good)
     plan.close()
