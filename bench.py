@@ -202,6 +202,7 @@ def run_safr(args):
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     launches = safr.safr_launches_per_frame(plan.handle)
     info = plan.info
+    stamps = []
 
     def one(i, trace):
         flush.fill_(float(i & 7))
@@ -212,6 +213,8 @@ def run_safr(args):
         e.record(stream)
         e.synchronize()
         ph = safr.safr_trace_read(plan.handle) if trace else None
+        if trace and launches == 1:
+            stamps.append(safr.safr_trace_phases(plan.handle))
         return s.elapsed_time(e), ph
 
     safr.safr_trace(plan.handle, True)
@@ -313,6 +316,8 @@ def run_safr(args):
                            "p99": lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
                            "mean": total_ms / args.steps},
             "kernels_ms": dict(zip(phase_names, ph_mean)), "path": "fused" if launches == 1 else "passes",
+            "fused_phases_us": ({k: float(np.median([st[k] for st in stamps])) for k in stamps[0]}
+                                if stamps else None),
             "frame_roofline": {"bytes": frame_bytes, "achieved_gbs": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9,
                                "peak_gbs": hbm, "frac": frame_bytes / (total_ms / args.steps * 1e-3) / 1e9 / hbm},
             "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,

@@ -204,6 +204,15 @@ safr_status safr_copy_B(safr_plan_t plan, int group, double *dst);
 safr_status safr_trace(safr_plan_t plan, int enable);
 safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
 
+/*
+ * Inside the last traced SAFR_PATH_FUSED frame, in microseconds from the
+ * first CTA's start (read from %globaltimer): when the last CTA finished
+ * phase 1, left grid barrier 1, finished phase 2, left barrier 2, finished
+ * phase 3, and the spread of the CTA start times.  Writes up to `n` values
+ * (6 in all; *n_out = 6).  SAFR_ERR_INVALID_ARG if no traced fused frame.
+ */
+safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out);
+
 /* Number of kernel launches one safr_reconstruct makes for this plan. */
 int safr_launches_per_frame(safr_plan_t plan);
 

@@ -42,7 +42,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 void free_plan_memory(safr_plan_s *p)
 {
     void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask, p->d_tt_w,
-                    p->d_xy_hat, p->d_pm, p->d_bar,
+                    p->d_xy_hat, p->d_pm, p->d_bar, p->d_stamps,
                     p->d_pre, p->d_status, p->d_in_stage, p->d_out_stage, p->d_in_scales_stage,
                     p->d_out_scales_stage};
     for (void *b : bufs)
@@ -561,6 +561,12 @@ safr_status safr_trace(safr_plan_t plan, int enable)
     if (enable && !plan->ev[0])
         for (auto &e : plan->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return SAFR_ERR_CUDA;
+    if (enable && !plan->d_stamps && plan->f_grid > 0) {
+        if (cudaMalloc((void **)&plan->d_stamps, (size_t)plan->f_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
+            return SAFR_ERR_OOM;
+        if (cudaMemset(plan->d_stamps, 0, (size_t)plan->f_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
+            return SAFR_ERR_CUDA;
+    }
     plan->trace = enable ? 1 : 0;
     plan->traced = 0;
     return SAFR_OK;
@@ -582,6 +588,35 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out)
 }
 
 int safr_launches_per_frame(safr_plan_t plan) { return plan ? safr::launches_per_frame(plan) : 0; }
+
+safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out)
+{
+    if (!plan || (!us && n > 0)) return SAFR_ERR_INVALID_ARG;
+    if (n_out) *n_out = 0;
+    if (!plan->traced || !safr::use_fused(plan) || !plan->d_stamps) return SAFR_ERR_INVALID_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return SAFR_ERR_CUDA;
+    if (cudaEventSynchronize(plan->ev[1]) != cudaSuccess) return SAFR_ERR_CUDA;
+    std::vector<unsigned long long> st((size_t)plan->f_grid * 6);
+    if (cudaMemcpy(st.data(), plan->d_stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return SAFR_ERR_CUDA;
+    // phases measured from the earliest CTA start: [0] phase 1 done (latest CTA),
+    // [1] barrier 1 released (latest), [2] phase 2 done (latest), [3] barrier 2
+    // released (latest), [4] phase 3 done (latest), [5] spread of CTA starts
+    unsigned long long t0 = ~0ull, tmax0 = 0, last[6] = {0};
+    for (int b = 0; b < plan->f_grid; ++b) {
+        t0 = std::min(t0, st[(size_t)b * 6]);
+        tmax0 = std::max(tmax0, st[(size_t)b * 6]);
+        for (int i = 1; i < 6; ++i) last[i] = std::max(last[i], st[(size_t)b * 6 + i]);
+    }
+    double v[6];
+    for (int i = 1; i < 6; ++i) v[i - 1] = 1e-3 * (double)(last[i] - t0);
+    v[5] = 1e-3 * (double)(tmax0 - t0);
+    for (int i = 0; i < 6 && i < n; ++i) us[i] = v[i];
+    if (n_out) *n_out = 6;
+    return SAFR_OK;
+}
 
 safr_status safr_set_path(safr_plan_t plan, int path)
 {

@@ -72,6 +72,7 @@ struct FusedParams {
     const C *xy_hat;      // [2][Mh][M] DFT2 of x*mask and y*mask (column k contiguous in j)
     R *pm;                // [G][P][2] per-row tip/tilt functionals
     unsigned *bar;        // [2] arrival count, generation
+    unsigned long long *stamps;  // [gridDim][6] phase timestamps (traced calls only)
     int *status;
     int star_tt[SAFR_MAX_G];
     GroupDev grp[2];
@@ -128,6 +129,8 @@ __global__ void __launch_bounds__(512, 1) k_frame(FusedParams<R> fp)
     const int M = fp.M, P = fp.P, Mh = fp.Mh, o = fp.o, L = fp.L, logM = fp.logM, G = fp.G;
     const int tid = threadIdx.x, nth = blockDim.x, b = blockIdx.x, nb = gridDim.x;
     const int lane = tid & 31, warp = tid >> 5, nwarps = nth >> 5;
+    unsigned long long *stamp = fp.stamps ? fp.stamps + (size_t)b * 6 : nullptr;
+    if (stamp && tid == 0) stamp[0] = globaltimer_ns();
     C *tw = (C *)smem;
     C *work = tw + M;  // phase scratch starts after the twiddles
 
@@ -209,7 +212,12 @@ __global__ void __launch_bounds__(512, 1) k_frame(FusedParams<R> fp)
         }
     }
     if (b == fp.skip_cta) return;  // test hook: the others' first barrier must time out
+    if (stamp) {
+        __syncthreads();
+        if (tid == 0) stamp[1] = globaltimer_ns();
+    }
     if (!grid_barrier(fp.bar, fp.status, fp.timeout_ns, &bar_flag)) return;
+    if (stamp && tid == 0) stamp[2] = globaltimer_ns();
 
     // ---- phase 2: columns --------------------------------------------------
     {
@@ -304,7 +312,12 @@ __global__ void __launch_bounds__(512, 1) k_frame(FusedParams<R> fp)
             }
         }
     }
+    if (stamp) {
+        __syncthreads();
+        if (tid == 0) stamp[3] = globaltimer_ns();
+    }
     if (!grid_barrier(fp.bar, fp.status, fp.timeout_ns, &bar_flag)) return;
+    if (stamp && tid == 0) stamp[4] = globaltimer_ns();
 
     // ---- phase 3: rows -----------------------------------------------------
     {
@@ -409,6 +422,7 @@ __global__ void __launch_bounds__(512, 1) k_frame(FusedParams<R> fp)
             __syncthreads();
         }
     }
+    if (stamp && tid == 0) stamp[5] = globaltimer_ns();
 }
 
 // ----------------------------------------------------------------------------
@@ -545,6 +559,7 @@ static FusedParams<R> fused_params(safr_plan_s *pl, const void *in, const float 
     fp.xy_hat = (const C *)pl->d_xy_hat;
     fp.pm = (R *)pl->d_pm;
     fp.bar = pl->d_bar;
+    fp.stamps = pl->trace ? pl->d_stamps : nullptr;
     fp.status = pl->d_status;
     for (int g = 0; g < pl->G; ++g) fp.star_tt[g] = pl->star_tt[g];
     for (int gi = 0; gi < pl->ngroups; ++gi) {

@@ -34,7 +34,7 @@ SAFR_PATH_AUTO, SAFR_PATH_FUSED, SAFR_PATH_PASSES = 0, 1, 2
 _PRECISION = {"fp32": SAFR_FP32, "fp16": SAFR_FP16_STORAGE, "fp64": SAFR_FP64}
 _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_reconstruct_host",
             "safr_get_status", "safr_get_plan_info", "safr_copy_B", "safr_trace", "safr_trace_read",
-            "safr_launches_per_frame", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
+            "safr_launches_per_frame", "safr_trace_phases", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
             "safr_destroy", "safr_status_string"]
 
 
@@ -89,6 +89,7 @@ def load(build_if_missing: bool = True):
     lib.safr_trace.argtypes = [vp, C.c_int]
     lib.safr_trace_read.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     lib.safr_launches_per_frame.argtypes = [vp]
+    lib.safr_trace_phases.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     lib.safr_set_path.argtypes = [vp, C.c_int]
     lib.safr_get_path.argtypes = [vp]
     lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
@@ -214,6 +215,15 @@ def safr_trace_read(plan: int):
     n = C.c_int(0)
     _check(load().safr_trace_read(plan, ms, 8, C.byref(n)), "safr_trace_read")
     return [ms[i] for i in range(n.value)]
+
+
+def safr_trace_phases(plan: int):
+    """Phase completion times (us) of the last traced persistent-kernel frame."""
+    us = (C.c_double * 8)()
+    n = C.c_int(0)
+    _check(load().safr_trace_phases(plan, us, 8, C.byref(n)), "safr_trace_phases")
+    keys = ["phase1_done", "barrier1_out", "phase2_done", "barrier2_out", "phase3_done", "start_spread"]
+    return dict(zip(keys, [us[i] for i in range(n.value)]))
 
 
 def safr_launches_per_frame(plan: int) -> int:
