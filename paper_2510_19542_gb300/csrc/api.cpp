@@ -42,7 +42,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 void free_plan_memory(safr_plan_s *p)
 {
     void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask, p->d_tt_w,
-                    p->d_xy_hat, p->d_pm, p->d_bar, p->d_stamps,
+                    p->d_xy_hat, p->d_pm, p->d_bar, p->d_stamps, p->d_twq,
                     p->d_pre, p->d_status, p->d_in_stage, p->d_out_stage, p->d_in_scales_stage,
                     p->d_out_scales_stage};
     for (void *b : bufs)
@@ -351,6 +351,19 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
             SAFR_TRY(upload((float2 **)&p->d_xy_hat, h));
         }
     }
+    {   // four-step twiddles W_M^(n1 k2) of the persistent kernel, from FP64
+        std::vector<double> tr, ti;
+        safr::frame2_twiddles(M, tr, ti);
+        if (p->precision == SAFR_FP64) {
+            std::vector<double2> h(M);
+            for (int i = 0; i < M; ++i) h[i] = make_double2(tr[i], ti[i]);
+            SAFR_TRY(upload((double2 **)&p->d_twq, h));
+        } else {
+            std::vector<float2> h(M);
+            for (int i = 0; i < M; ++i) h[i] = make_float2((float)tr[i], (float)ti[i]);
+            SAFR_TRY(upload((float2 **)&p->d_twq, h));
+        }
+    }
     SAFR_TRY(cudaMalloc(&p->d_pm, (size_t)p->G * p->P * 2 * rs));
     SAFR_TRY(cudaMemset(p->d_pm, 0, (size_t)p->G * p->P * 2 * rs));
     SAFR_TRY(cudaMalloc((void **)&p->d_bar, 2 * sizeof(unsigned)));
@@ -561,10 +574,10 @@ safr_status safr_trace(safr_plan_t plan, int enable)
     if (enable && !plan->ev[0])
         for (auto &e : plan->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return SAFR_ERR_CUDA;
-    if (enable && !plan->d_stamps && plan->f_grid > 0) {
-        if (cudaMalloc((void **)&plan->d_stamps, (size_t)plan->f_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
+    if (enable && !plan->d_stamps && plan->f2_grid > 0) {
+        if (cudaMalloc((void **)&plan->d_stamps, (size_t)plan->f2_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
             return SAFR_ERR_OOM;
-        if (cudaMemset(plan->d_stamps, 0, (size_t)plan->f_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
+        if (cudaMemset(plan->d_stamps, 0, (size_t)plan->f2_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
             return SAFR_ERR_CUDA;
     }
     plan->trace = enable ? 1 : 0;
@@ -597,7 +610,7 @@ safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out)
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
     if (cudaEventSynchronize(plan->ev[1]) != cudaSuccess) return SAFR_ERR_CUDA;
-    std::vector<unsigned long long> st((size_t)plan->f_grid * 6);
+    std::vector<unsigned long long> st((size_t)plan->f2_grid * 6);
     if (cudaMemcpy(st.data(), plan->d_stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
         return SAFR_ERR_CUDA;
@@ -605,7 +618,7 @@ safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out)
     // [1] barrier 1 released (latest), [2] phase 2 done (latest), [3] barrier 2
     // released (latest), [4] phase 3 done (latest), [5] spread of CTA starts
     unsigned long long t0 = ~0ull, tmax0 = 0, last[6] = {0};
-    for (int b = 0; b < plan->f_grid; ++b) {
+    for (int b = 0; b < plan->f2_grid; ++b) {
         t0 = std::min(t0, st[(size_t)b * 6]);
         tmax0 = std::max(tmax0, st[(size_t)b * 6]);
         for (int i = 1; i < 6; ++i) last[i] = std::max(last[i], st[(size_t)b * 6 + i]);

@@ -1,0 +1,48 @@
+// Per-precision instantiation and dispatch of the persistent frame kernel:
+// one instance per supported grid size M (compile-time FFT shapes).
+#pragma once
+
+#include "frame_impl.cuh"
+
+namespace safr {
+
+template <typename R, typename TIN, typename TOUT, int M>
+struct Frame2Inst {
+    static void *kernel() { return (void *)k_frame2<M, R, TIN, TOUT>; }
+    static bool configure(safr_plan_s *pl, int nsm) { return Frame2Host<M, R>::configure(pl, nsm, kernel()); }
+    static cudaError_t launch(safr_plan_s *pl, const void *in, const float *isc, void *out, float *osc,
+                              cudaStream_t st)
+    {
+        Frame2Params<R> fp = Frame2Host<M, R>::params(pl, in, isc, out, osc);
+        void *args[] = {&fp};
+        return cudaLaunchCooperativeKernel(kernel(), dim3(pl->f2_grid), dim3(512), args, pl->f2_smem, st);
+    }
+};
+
+// Walks the compile-time list of grid sizes.
+template <typename R, typename TIN, typename TOUT, int... Ms>
+struct Frame2Table;
+template <typename R, typename TIN, typename TOUT>
+struct Frame2Table<R, TIN, TOUT> {
+    static bool configure(safr_plan_s *, int) { return false; }
+    static cudaError_t launch(safr_plan_s *, const void *, const float *, void *, float *, cudaStream_t)
+    {
+        return cudaErrorInvalidValue;
+    }
+};
+template <typename R, typename TIN, typename TOUT, int M0, int... Ms>
+struct Frame2Table<R, TIN, TOUT, M0, Ms...> {
+    static bool configure(safr_plan_s *pl, int nsm)
+    {
+        if (pl->M == M0) return Frame2Inst<R, TIN, TOUT, M0>::configure(pl, nsm);
+        return Frame2Table<R, TIN, TOUT, Ms...>::configure(pl, nsm);
+    }
+    static cudaError_t launch(safr_plan_s *pl, const void *in, const float *isc, void *out, float *osc,
+                              cudaStream_t st)
+    {
+        if (pl->M == M0) return Frame2Inst<R, TIN, TOUT, M0>::launch(pl, in, isc, out, osc, st);
+        return Frame2Table<R, TIN, TOUT, Ms...>::launch(pl, in, isc, out, osc, st);
+    }
+};
+
+}  // namespace safr

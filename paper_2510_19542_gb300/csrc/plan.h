@@ -92,9 +92,11 @@ struct safr_plan_s {
     int pdl = 1;  // programmatic dependent launch between the three passes
     int path = SAFR_PATH_AUTO;  // requested kernel schedule
     int fused_ok = 0;           // the persistent kernel fits this plan
-    // persistent-kernel shapes
-    int f_grid = 0, f_npr = 0, f_n1 = 0, f_lchunk = 1, f_rt3 = 2, f_stage3 = 2, f_sp3 = 1, f_tiles3 = 1, f_n3 = 1;
-    size_t f_smem = 0;
+    // persistent-kernel shapes (frame_impl.cuh)
+    int f2_grid = 0, f2_stage_b = 0, f2_rt3 = 2, f2_tiles3 = 1, f2_n3 = 1, f2_cap3 = 1;
+    int f2_st3[2] = {0, 0}, f2_nsrc3[2] = {0, 0};
+    unsigned f2_off_b = 0, f2_off_s12 = 0, f2_off_s3 = 0;
+    size_t f2_smem = 0;
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
     int gmax = 16; // compile-time bound on stars per group of the column pass
@@ -112,6 +114,7 @@ struct safr_plan_s {
     void *d_rs_w = nullptr;
     unsigned char *d_mask = nullptr;
     void *d_tt_w = nullptr;
+    void *d_twq = nullptr;     // [M] four-step twiddles of the persistent kernel
     void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT)
     void *d_pm = nullptr;      // [G][P][2] per-row tip/tilt functionals
     unsigned *d_bar = nullptr; // grid barrier words
@@ -138,6 +141,7 @@ int launches_per_frame(const safr_plan_s *plan);
 bool configure_fused(safr_plan_s *plan);
 cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scales, void *out, float *out_scales,
                          cudaStream_t stream);
+void frame2_twiddles(int M, std::vector<double> &re, std::vector<double> &im);
 inline bool use_fused(const safr_plan_s *plan)
 {
     return plan->fused_ok && plan->path != SAFR_PATH_PASSES;
