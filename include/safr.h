@@ -206,10 +206,13 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
 
 /*
  * Inside the last traced SAFR_PATH_FUSED frame, in microseconds from the
- * first CTA's start (read from %globaltimer): when the last CTA finished
- * phase 1, left grid barrier 1, finished phase 2, left barrier 2, finished
- * phase 3, and the spread of the CTA start times.  Writes up to `n` values
- * (6 in all; *n_out = 6).  SAFR_ERR_INVALID_ARG if no traced fused frame.
+ * first CTA's start (read from %globaltimer), the time the last CTA reached
+ * each of 11 marks: 0 start, 1 prologue done, 2 first phase-1 transforms done,
+ * 3 phase 1 done, 4 out of grid barrier 1, 5 first column's forward
+ * transforms done, 6 phase 2 done, 7 out of grid barrier 2, 8 first phase-3
+ * tile staged, 9 its transforms done, 10 phase 3 done (0 for a mark no CTA
+ * reached).  Writes up to `n` values; *n_out = 11.  SAFR_ERR_INVALID_ARG if
+ * there is no traced persistent-kernel frame.
  */
 safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out);
 

@@ -575,10 +575,9 @@ safr_status safr_trace(safr_plan_t plan, int enable)
         for (auto &e : plan->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return SAFR_ERR_CUDA;
     if (enable && !plan->d_stamps && plan->f2_grid > 0) {
-        if (cudaMalloc((void **)&plan->d_stamps, (size_t)plan->f2_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
-            return SAFR_ERR_OOM;
-        if (cudaMemset(plan->d_stamps, 0, (size_t)plan->f2_grid * 6 * sizeof(unsigned long long)) != cudaSuccess)
-            return SAFR_ERR_CUDA;
+        const size_t nst = (size_t)plan->f2_grid * SAFR_TRACE_MARKS * sizeof(unsigned long long);
+        if (cudaMalloc((void **)&plan->d_stamps, nst) != cudaSuccess) return SAFR_ERR_OOM;
+        if (cudaMemset(plan->d_stamps, 0, nst) != cudaSuccess) return SAFR_ERR_CUDA;
     }
     plan->trace = enable ? 1 : 0;
     plan->traced = 0;
@@ -610,24 +609,23 @@ safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out)
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
     if (cudaEventSynchronize(plan->ev[1]) != cudaSuccess) return SAFR_ERR_CUDA;
-    std::vector<unsigned long long> st((size_t)plan->f2_grid * 6);
+    const int K = SAFR_TRACE_MARKS;
+    std::vector<unsigned long long> st((size_t)plan->f2_grid * K);
     if (cudaMemcpy(st.data(), plan->d_stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
         return SAFR_ERR_CUDA;
-    // phases measured from the earliest CTA start: [0] phase 1 done (latest CTA),
-    // [1] barrier 1 released (latest), [2] phase 2 done (latest), [3] barrier 2
-    // released (latest), [4] phase 3 done (latest), [5] spread of CTA starts
-    unsigned long long t0 = ~0ull, tmax0 = 0, last[6] = {0};
-    for (int b = 0; b < plan->f2_grid; ++b) {
-        t0 = std::min(t0, st[(size_t)b * 6]);
-        tmax0 = std::max(tmax0, st[(size_t)b * 6]);
-        for (int i = 1; i < 6; ++i) last[i] = std::max(last[i], st[(size_t)b * 6 + i]);
+    // mark i: latest CTA to reach it, in microseconds from the earliest CTA start
+    // (marks a CTA never reaches, e.g. a CTA with no phase-2 column, stay 0)
+    unsigned long long t0 = ~0ull;
+    for (int b = 0; b < plan->f2_grid; ++b) t0 = std::min(t0, st[(size_t)b * K]);
+    double v[SAFR_TRACE_MARKS];
+    for (int i = 0; i < K; ++i) {
+        unsigned long long last = 0;
+        for (int b = 0; b < plan->f2_grid; ++b) last = std::max(last, st[(size_t)b * K + i]);
+        v[i] = last > t0 ? 1e-3 * (double)(last - t0) : 0.0;
     }
-    double v[6];
-    for (int i = 1; i < 6; ++i) v[i - 1] = 1e-3 * (double)(last[i] - t0);
-    v[5] = 1e-3 * (double)(tmax0 - t0);
-    for (int i = 0; i < 6 && i < n; ++i) us[i] = v[i];
-    if (n_out) *n_out = 6;
+    for (int i = 0; i < K && i < n; ++i) us[i] = v[i];
+    if (n_out) *n_out = K;
     return SAFR_OK;
 }
 

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     const int tid = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int slot = tid / R1, t = tid % R1;
-    unsigned long long *stamp = fp.stamps ? fp.stamps + (size_t)b * 6 : nullptr;
+    unsigned long long *stamp = fp.stamps ? fp.stamps + (size_t)b * SAFR_TRACE_MARKS : nullptr;
     if (stamp && tid == 0) stamp[0] = gtimer();
 
     C *twq = (C *)smem;                      // [M]
@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     }
     for (int i = tid; i < M; i += NTH) twq[i] = fp.twq[i];
     __syncthreads();
+    if (stamp && tid == 0) stamp[1] = gtimer();
 
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
     auto drain = [&]() {
@@ -298,6 +299,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                     for (int k1 = 0; k1 < R1; ++k1) Z[(size_t)slot * M + t + c * R1 + R2 * k1] = out[c][k1];
             }
             __syncthreads();
+            if (stamp && tid == 0 && base == lo) stamp[2] = gtimer();
             // X1 = (Z[k] + conj Z[M-k]) / 2, X2 = (Z[k] - conj Z[M-k]) / 2i, row pair fastest
             for (int idx = tid; idx < nact * Mh; idx += NTH) {
                 const int k = idx / nact, i = idx - k * nact;
@@ -317,13 +319,13 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     }
     if (stamp) {
         __syncthreads();
-        if (tid == 0) stamp[1] = gtimer();
+        if (tid == 0) stamp[3] = gtimer();
     }
     if (!grid_sync_bounded(fp.bar, fp.status, fp.timeout_ns, &bar_flag)) {
         drain();
         return;
     }
-    if (stamp && tid == 0) stamp[2] = gtimer();
+    if (stamp && tid == 0) stamp[4] = gtimer();
 
     // ---- phase 2: columns --------------------------------------------------------
     {
@@ -385,6 +387,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 }
                 __syncthreads();
             }
+            if (stamp && tid == 0 && k == b) stamp[5] = gtimer();
             const C *Bcol;
             if (fp.stage_b) {
                 if (tid == 0 && !mbar_wait_bounded(&mbar, tma_phase, fp.timeout_ns, fp.status)) bar_flag = -1;
@@ -462,13 +465,13 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     }
     if (stamp) {
         __syncthreads();
-        if (tid == 0) stamp[3] = gtimer();
+        if (tid == 0) stamp[6] = gtimer();
     }
     if (!grid_sync_bounded(fp.bar, fp.status, fp.timeout_ns, &bar_flag)) {
         drain();
         return;
     }
-    if (stamp && tid == 0) stamp[4] = gtimer();
+    if (stamp && tid == 0) stamp[7] = gtimer();
 
     // ---- phase 3: (layer, row tile) ----------------------------------------------
     {
@@ -514,6 +517,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 }
             }
             __syncthreads();
+            if (stamp && tid == 0 && it == b) stamp[8] = gtimer();
             // complex-to-real transforms of row pairs, both groups in one batch
             const int ntot = npair0 + npair1;
             for (int base = 0; base < ntot; base += fp.cap3) {
@@ -565,6 +569,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 }
                 __syncthreads();
             }
+            if (stamp && tid == 0 && it == b) stamp[9] = gtimer();
             R inv_scale = R(1);
             if (fp.out_scales) {
                 // layer energy sum_n |b(n)|^2 over the groups (fixed order) -> mean square / M^4
@@ -600,7 +605,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
             __syncthreads();
         }
     }
-    if (stamp && tid == 0) stamp[5] = gtimer();
+    if (stamp && tid == 0) stamp[10] = gtimer();
 }
 
 // ----------------------------------------------------------------------------

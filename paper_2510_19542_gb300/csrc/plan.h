@@ -9,6 +9,9 @@
 
 #include "safr.h"
 
+// timestamps a traced persistent-kernel frame records per CTA
+#define SAFR_TRACE_MARKS 11
+
 namespace safr {
 
 // One star group of the split tomography (Section 3.3): all LGS stars, or all
@@ -118,7 +121,7 @@ struct safr_plan_s {
     void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT)
     void *d_pm = nullptr;      // [G][P][2] per-row tip/tilt functionals
     unsigned *d_bar = nullptr; // grid barrier words
-    unsigned long long *d_stamps = nullptr;  // [grid][6] phase timestamps of traced fused frames
+    unsigned long long *d_stamps = nullptr;  // [grid][SAFR_TRACE_MARKS] timestamps of traced fused frames
     double *d_pre = nullptr;  // shifts, sw, tau of both groups (precompute)
     int *d_status = nullptr;
     void *d_in_stage = nullptr, *d_out_stage = nullptr;

@@ -219,10 +219,11 @@ def safr_trace_read(plan: int):
 
 def safr_trace_phases(plan: int):
     """Phase completion times (us) of the last traced persistent-kernel frame."""
-    us = (C.c_double * 8)()
+    us = (C.c_double * 16)()
     n = C.c_int(0)
-    _check(load().safr_trace_phases(plan, us, 8, C.byref(n)), "safr_trace_phases")
-    keys = ["phase1_done", "barrier1_out", "phase2_done", "barrier2_out", "phase3_done", "start_spread"]
+    _check(load().safr_trace_phases(plan, us, 16, C.byref(n)), "safr_trace_phases")
+    keys = ["start", "prologue", "p1_first_fft", "p1_done", "bar1_out", "p2_fwd", "p2_done", "bar2_out",
+            "p3_staged", "p3_fft", "p3_done"]
     return dict(zip(keys, [us[i] for i in range(n.value)]))
 
 
