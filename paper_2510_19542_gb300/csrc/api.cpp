@@ -366,8 +366,8 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     }
     SAFR_TRY(cudaMalloc(&p->d_pm, (size_t)p->G * p->P * 2 * rs));
     SAFR_TRY(cudaMemset(p->d_pm, 0, (size_t)p->G * p->P * 2 * rs));
-    SAFR_TRY(cudaMalloc((void **)&p->d_bar, 2 * sizeof(unsigned)));
-    SAFR_TRY(cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned)));
+    SAFR_TRY(cudaMalloc((void **)&p->d_bar, 2 * sizeof(unsigned long long)));
+    SAFR_TRY(cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned long long)));
 
     // precompute inputs: per group sx, sy [G][L], sw [L], tau [L]
     std::vector<double> pre;
@@ -505,7 +505,7 @@ safr_status safr_get_status(safr_plan_t plan)
     if (st != 0) {
         // clear the sticky word and re-arm the grid barrier that a timeout left half-counted
         if (cudaMemset(plan->d_status, 0, sizeof(int)) != cudaSuccess) return SAFR_ERR_CUDA;
-        if (cudaMemset(plan->d_bar, 0, 2 * sizeof(unsigned)) != cudaSuccess) return SAFR_ERR_CUDA;
+        if (cudaMemset(plan->d_bar, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return SAFR_ERR_CUDA;
         if (cudaDeviceSynchronize() != cudaSuccess) return SAFR_ERR_CUDA;
     }
     return (safr_status)st;

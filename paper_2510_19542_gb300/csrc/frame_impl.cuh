@@ -79,7 +79,7 @@ struct Frame2Params {
     const R *tt_w;             // [2][P][P]
     const C *xy_hat;           // [2][M/2][M]
     R *pm;                     // [G][P][2]
-    unsigned *bar;             // [2]
+    unsigned long long *bar;   // [2] arrival count, launch epoch
     unsigned long long *stamps;
     int *status;
     int star_tt[SAFR_MAX_G];
@@ -141,23 +141,31 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parit
     return true;
 }
 
-// Grid-wide barrier of the cooperative launch; false if it timed out.
-__device__ __forceinline__ bool grid_sync_bounded(unsigned *bar, int *status, unsigned long long timeout_ns, int *flag)
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier number `which` (0, 1) of the cooperative launch with epoch
+// `epoch`.  bar[0] counts arrivals over the plan's lifetime: every launch adds
+// 2 * gridDim.x, so barrier `which` of epoch E is complete when the count
+// reaches (2E + which + 1) * gridDim.x.  Arrival is one release reduction (no
+// round trip); one thread per CTA polls with acquire loads until the count is
+// reached or the time limit passes.  Returns false (SAFR_ERR_TIMEOUT recorded)
+// on a timeout.
+__device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsigned long long epoch, int which,
+                                                  int *status, unsigned long long timeout_ns, int *flag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = bar + 1;
-        const unsigned gen = *vgen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u);
+        const unsigned long long target = (2ull * epoch + (unsigned long long)which + 1ull) * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
+        if (ld_acquire_u64(bar) < target) {
             const unsigned long long t0 = gtimer();
-            while (*vgen == gen) {
+            while (ld_acquire_u64(bar) < target) {
                 if (gtimer() - t0 > timeout_ns) {
                     atomicExch(status, (int)SAFR_ERR_TIMEOUT);
                     ok = 0;
@@ -165,7 +173,6 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned *bar, int *status, un
                 }
             }
         }
-        __threadfence();
         *flag = ok;
     }
     __syncthreads();
@@ -177,22 +184,25 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
 {
     using C = typename Frame2Params<R>::C;
     using S = FftShape<M>;
-    constexpr int R1 = S::R1, R2 = S::R2, CB = S::CB, TS = S::TS;
+    constexpr int TS = S::TS;
     constexpr int Mh = M / 2;
+    constexpr int LOGM = S::LOG;
     constexpr int NTH = 512;
-    constexpr int SLOTS = NTH / R1;
+    constexpr int SLOTS = NTH / S::R1;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int bar_flag;
+    __shared__ unsigned long long epoch_s;
     __shared__ R tt_b[SAFR_MAX_G], tt_c[SAFR_MAX_G];
     __shared__ R red[32];
 
     const int P = fp.P, o = fp.o, L = fp.L, G = fp.G;
     const int tid = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const int slot = tid / R1, t = tid % R1;
     unsigned long long *stamp = fp.stamps ? fp.stamps + (size_t)b * SAFR_TRACE_MARKS : nullptr;
     if (stamp && tid == 0) stamp[0] = gtimer();
+    // epoch of this launch: advanced by CTA 0 once every CTA is past the last barrier
+    if (tid == 0) epoch_s = ld_acquire_u64(fp.bar + 1);
 
     C *twq = (C *)smem;                      // [M]
     C *Bs = (C *)(smem + fp.off_b);          // staged B column block
@@ -205,14 +215,20 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     unsigned tma_phase = 0;
     bool tma_pending = false;
     if (tid == 0 && fp.stage_b) mbar_init(&mbar, 1);
-    __syncthreads();
-    if (fp.stage_b && b < Mh && tid == 0) {
-        const C *src = fp.B + (size_t)b * colB;
-        mbar_expect_tx(&mbar, colB_bytes);
-        for (unsigned off = 0; off < colB_bytes; off += 32768u)
-            tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off, min(32768u, colB_bytes - off), &mbar);
-    }
-    if (fp.stage_b && b < Mh) tma_pending = true;
+    // B of the first column is requested once this CTA's phase-1 input has
+    // arrived, so the 20+ MB stream does not queue ahead of those loads
+    auto issue_first_b = [&]() {
+        if (fp.stage_b && b < Mh && !tma_pending) {
+            if (tid == 0) {
+                const C *src = fp.B + (size_t)b * colB;
+                mbar_expect_tx(&mbar, colB_bytes);
+                for (unsigned off = 0; off < colB_bytes; off += 32768u)
+                    tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off,
+                                min(32768u, colB_bytes - off), &mbar);
+            }
+            tma_pending = true;
+        }
+    };
     {   // later columns of this CTA (or every column when B is not staged): into L2
         const int k0 = fp.stage_b ? b + nb : b;
         for (int k = k0; k < Mh; k += nb) {
@@ -222,7 +238,6 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
         }
     }
     for (int i = tid; i < M; i += NTH) twq[i] = fp.twq[i];
-    __syncthreads();
     if (stamp && tid == 0) stamp[1] = gtimer();
 
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
@@ -233,79 +248,66 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     // ---- phase 1: row pairs ----------------------------------------------------
     {
         const int lo = (int)(((long long)b * fp.n1) / nb), hi = (int)(((long long)(b + 1) * fp.n1) / nb);
-        const int cap1 = min(SLOTS, (fp.n1 + nb - 1) / nb);  // row pairs in flight
-        C *T = (C *)s12;                               // [cap1][TS]
-        C *Z = T + (size_t)cap1 * TS;                  // [cap1][M]
-        const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
+        const int cap1 = min(SLOTS, (fp.n1 + nb - 1) / nb);  // row pairs per batch
+        C *X = (C *)s12;                                      // [cap1][TS]
         for (int base = lo; base < hi; base += cap1) {
             const int nact = min(cap1, hi - base);
-            const int item = base + slot;
-            const bool act = slot < nact;
-            int g = 0, a0 = 0;
-            if (act) {
-                g = item / fp.npr;
-                a0 = 2 * (item - g * fp.npr);
-            }
-            const bool two = act && a0 + 1 < P;
-            const bool tt = act && fp.star_tt[g];
-            C v[R2];
-            R sb0 = 0, sc0 = 0, sb1 = 0, sc1 = 0;
-            const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
-            const R sc = (act && fp.in_scales) ? (R)fp.in_scales[g] : R(1);
-#pragma unroll
-            for (int n2 = 0; n2 < R2; ++n2) {
-                const int qq = t + R1 * n2 - o;
+            // z[q] = psi[row a0][q - o] + i psi[row a0 + 1][q - o], zero outside the pupil
+            for (int idx = tid; idx < (nact << LOGM); idx += NTH) {
+                const int i = idx >> LOGM, q = idx & (M - 1);
+                const int item = base + i, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
+                const int qq = q - o;
                 R re = 0, im = 0;
-                if (act && qq >= 0 && qq < P) {
+                if (qq >= 0 && qq < P) {
+                    const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
+                    const R sc = fp.in_scales ? (R)fp.in_scales[g] : R(1);
                     re = load_in<R>(psi + (size_t)a0 * P + qq) * sc;
-                    if (two) im = load_in<R>(psi + (size_t)(a0 + 1) * P + qq) * sc;
-                    if (tt) {
-                        sb0 += wb[a0 * P + qq] * re;
-                        sc0 += wc[a0 * P + qq] * re;
-                        if (two) {
-                            sb1 += wb[(a0 + 1) * P + qq] * im;
-                            sc1 += wc[(a0 + 1) * P + qq] * im;
+                    if (a0 + 1 < P) im = load_in<R>(psi + (size_t)(a0 + 1) * P + qq) * sc;
+                }
+                X[(size_t)i * TS + q] = C{re, im};
+            }
+            __syncthreads();
+            issue_first_b();
+            // per-row shares of the tip/tilt functionals (one warp per row pair)
+            if (fp.any_tt)
+                for (int i = warp; i < nact; i += NTH / 32) {
+                    const int item = base + i, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
+                    if (!fp.star_tt[g]) continue;
+                    const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
+                    R s0b = 0, s0c = 0, s1b = 0, s1c = 0;
+                    for (int q = lane; q < P; q += 32) {
+                        const C v = X[(size_t)i * TS + o + q];
+                        s0b += wb[a0 * P + q] * v.x;
+                        s0c += wc[a0 * P + q] * v.x;
+                        if (a0 + 1 < P) {
+                            s1b += wb[(a0 + 1) * P + q] * v.y;
+                            s1c += wc[(a0 + 1) * P + q] * v.y;
+                        }
+                    }
+                    for (int off = 16; off > 0; off >>= 1) {
+                        s0b += __shfl_xor_sync(0xffffffffu, s0b, off);
+                        s0c += __shfl_xor_sync(0xffffffffu, s0c, off);
+                        s1b += __shfl_xor_sync(0xffffffffu, s1b, off);
+                        s1c += __shfl_xor_sync(0xffffffffu, s1c, off);
+                    }
+                    if (lane == 0) {
+                        R *d = fp.pm + ((size_t)g * P + a0) * 2;
+                        d[0] = s0b;
+                        d[1] = s0c;
+                        if (a0 + 1 < P) {
+                            d[2] = s1b;
+                            d[3] = s1c;
                         }
                     }
                 }
-                v[n2] = C{re, im};
-            }
-            if (fp.any_tt) {
-#pragma unroll
-                for (int off = R1 / 2; off > 0; off >>= 1) {
-                    sb0 += __shfl_xor_sync(0xffffffffu, sb0, off);
-                    sc0 += __shfl_xor_sync(0xffffffffu, sc0, off);
-                    sb1 += __shfl_xor_sync(0xffffffffu, sb1, off);
-                    sc1 += __shfl_xor_sync(0xffffffffu, sc1, off);
-                }
-                if (tt && t == 0) {
-                    R *d = fp.pm + ((size_t)g * P + a0) * 2;
-                    d[0] = sb0;
-                    d[1] = sc0;
-                    if (two) {
-                        d[2] = sb1;
-                        d[3] = sc1;
-                    }
-                }
-            }
-            if (act) fft_step_a<M, false>(v, t, T + (size_t)slot * TS, twq);
-            __syncthreads();
-            if (act) {
-                C out[CB][R1];
-                fft_step_b<M, false>(out, t, T + (size_t)slot * TS);
-#pragma unroll
-                for (int c = 0; c < CB; ++c)
-#pragma unroll
-                    for (int k1 = 0; k1 < R1; ++k1) Z[(size_t)slot * M + t + c * R1 + R2 * k1] = out[c][k1];
-            }
-            __syncthreads();
+            fft_core<M>(X, nact, 0, twq);
             if (stamp && tid == 0 && base == lo) stamp[2] = gtimer();
             // X1 = (Z[k] + conj Z[M-k]) / 2, X2 = (Z[k] - conj Z[M-k]) / 2i, row pair fastest
             for (int idx = tid; idx < nact * Mh; idx += NTH) {
                 const int k = idx / nact, i = idx - k * nact;
                 const int it2 = base + i, g2 = it2 / fp.npr, b0 = 2 * (it2 - g2 * fp.npr);
-                const C z = Z[(size_t)i * M + k];
-                const C zc = Z[(size_t)i * M + ((M - k) & (M - 1))];
+                const C z = X[(size_t)i * TS + k];
+                const C zc = X[(size_t)i * TS + ((M - k) & (M - 1))];
                 C *dst = fp.w1 + ((size_t)g2 * Mh + k) * P + b0;
                 dst[0] = C{R(0.5) * (z.x + zc.x), R(0.5) * (z.y - zc.y)};
                 if (b0 + 1 < P) dst[1] = C{R(0.5) * (z.y + zc.y), R(0.5) * (zc.x - z.x)};
@@ -313,6 +315,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
             __syncthreads();
         }
     }
+    issue_first_b();  // CTAs without phase-1 rows
     if (b == fp.skip_cta) {  // test hook: every other CTA's first barrier must time out
         drain();
         return;
@@ -321,7 +324,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
         __syncthreads();
         if (tid == 0) stamp[3] = gtimer();
     }
-    if (!grid_sync_bounded(fp.bar, fp.status, fp.timeout_ns, &bar_flag)) {
+    if (!grid_sync_bounded(fp.bar, epoch_s, 0, fp.status, fp.timeout_ns, &bar_flag)) {
         drain();
         return;
     }
@@ -346,52 +349,33 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 tt_c[g] = sc;
             }
         }
-        C *D = (C *)s12;                 // [G][M] spectra d_g(j) of the column
-        C *T = D + (size_t)G * M;        // [SLOTS][TS]
-        __syncthreads();
+        const int cap2 = min(SLOTS, fp.ntask2);
+        C *D = (C *)s12;                  // [G][TS] spectra d_g(j) of the column
+        C *Y = D + (size_t)G * TS;        // [cap2][TS] layer spectra -> inverse transforms
         for (int k = b; k < Mh; k += nb) {
-            // forward FFT of each star's column (p = t + R1 n2), zero outside the pupil
-            for (int base = 0; base < G; base += SLOTS) {
-                const int s = base + slot;
-                const bool act = s < G;
-                if (act) {
-                    C v[R2];
-                    const C *col = fp.w1 + ((size_t)s * Mh + k) * P;
-#pragma unroll
-                    for (int n2 = 0; n2 < R2; ++n2) {
-                        const int pp = t + R1 * n2 - o;
-                        v[n2] = (pp >= 0 && pp < P) ? __ldcg(col + pp) : C{0, 0};
-                    }
-                    fft_step_a<M, false>(v, t, T + (size_t)slot * TS, twq);
-                }
-                __syncthreads();
-                if (act) {
-                    C out[CB][R1];
-                    fft_step_b<M, false>(out, t, T + (size_t)slot * TS);
-                    const bool tt = fp.star_tt[s] != 0;
-                    const R tb = tt ? tt_b[s] : R(0), tc = tt ? tt_c[s] : R(0);
-#pragma unroll
-                    for (int c = 0; c < CB; ++c)
-#pragma unroll
-                        for (int k1 = 0; k1 < R1; ++k1) {
-                            const int j = t + c * R1 + R2 * k1;
-                            C d = out[c][k1];
-                            if (tt) {
-                                const C xh = fp.xy_hat[(size_t)k * M + j];
-                                const C yh = fp.xy_hat[(size_t)(Mh + k) * M + j];
-                                d.x -= tb * xh.x + tc * yh.x;
-                                d.y -= tb * xh.y + tc * yh.y;
-                            }
-                            D[(size_t)s * M + j] = d;
-                        }
+            // every star's column of w1, zero-padded (p contiguous: coalesced)
+            for (int idx = tid; idx < (G << LOGM); idx += NTH) {
+                const int s = idx >> LOGM, p = idx & (M - 1), pp = p - o;
+                D[(size_t)s * TS + p] = (pp >= 0 && pp < P) ? __ldcg(fp.w1 + ((size_t)s * Mh + k) * P + pp) : C{0, 0};
+            }
+            __syncthreads();
+            for (int base = 0; base < G; base += SLOTS) fft_core<M>(D + (size_t)base * TS, min(SLOTS, G - base), 0, twq);
+            if (fp.any_tt) {  // d_g -= b_g X(j, k) + c_g Y(j, k) for the LGS stars
+                for (int idx = tid; idx < (G << LOGM); idx += NTH) {
+                    const int s = idx >> LOGM, j = idx & (M - 1);
+                    if (!fp.star_tt[s]) continue;
+                    const C xh = fp.xy_hat[((size_t)k << LOGM) + j];
+                    const C yh = fp.xy_hat[((size_t)(Mh + k) << LOGM) + j];
+                    C &d = D[(size_t)s * TS + j];
+                    d.x -= tt_b[s] * xh.x + tt_c[s] * yh.x;
+                    d.y -= tt_b[s] * xh.y + tt_c[s] * yh.y;
                 }
                 __syncthreads();
             }
             if (stamp && tid == 0 && k == b) stamp[5] = gtimer();
             const C *Bcol;
             if (fp.stage_b) {
-                if (tid == 0 && !mbar_wait_bounded(&mbar, tma_phase, fp.timeout_ns, fp.status)) bar_flag = -1;
-                else if (tid == 0) bar_flag = 1;
+                if (tid == 0) bar_flag = mbar_wait_bounded(&mbar, tma_phase, fp.timeout_ns, fp.status) ? 1 : -1;
                 __syncthreads();
                 tma_pending = false;
                 tma_phase ^= 1u;
@@ -400,78 +384,69 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
             } else {
                 Bcol = fp.B + (size_t)k * colB;
             }
-            // per-frequency apply straight into the inverse FFT along j
-            for (int base = 0; base < fp.ntask2; base += SLOTS) {
-                const int task = base + slot;
-                const bool act = task < fp.ntask2;
-                int gi = 0, l = 0;
-                if (act) {
-                    gi = task / L;
-                    l = task - gi * L;
-                }
-                R en = 0;
-                if (act) {
+            // b_l(j) = sum_g B_lg(j) d_g(j) for each (group, layer), then inverse transforms along j
+            for (int base = 0; base < fp.ntask2; base += cap2) {
+                const int nact = min(cap2, fp.ntask2 - base);
+                for (int idx = tid; idx < (nact << LOGM); idx += NTH) {
+                    const int i = idx >> LOGM, j = idx & (M - 1);
+                    const int task = base + i, gi = task / L, l = task - gi * L;
                     const GroupDev &gr = fp.grp[gi];
-                    const int Gg = gr.G;
-                    const C *Bl = Bcol + (size_t)(gr.b_row0 + l * Gg) * M;
-                    C acc[R2];
-#pragma unroll
-                    for (int n2 = 0; n2 < R2; ++n2) acc[n2] = C{0, 0};
-                    for (int gg = 0; gg < Gg; ++gg) {
-                        const C *Brow = Bl + (size_t)gg * M + t;
-                        const C *Drow = D + (size_t)gr.star[gg] * M + t;
-#pragma unroll
-                        for (int n2 = 0; n2 < R2; ++n2) {
-                            const C bv = Brow[R1 * n2];
-                            const C dv = Drow[R1 * n2];
-                            acc[n2].x += bv.x * dv.x - bv.y * dv.y;
-                            acc[n2].y += bv.x * dv.y + bv.y * dv.x;
-                        }
+                    const C *Bj = Bcol + ((size_t)(gr.b_row0 + l * gr.G) << LOGM) + j;
+                    R ar = 0, ai = 0;
+                    for (int gg = 0; gg < gr.G; ++gg) {
+                        const C bv = Bj[(size_t)gg << LOGM];
+                        const C dv = D[(size_t)gr.star[gg] * TS + j];
+                        ar += bv.x * dv.x - bv.y * dv.y;
+                        ai += bv.x * dv.y + bv.y * dv.x;
                     }
-                    if (fp.energy) {
-#pragma unroll
-                        for (int n2 = 0; n2 < R2; ++n2) en += acc[n2].x * acc[n2].x + acc[n2].y * acc[n2].y;
-                    }
-                    fft_step_a<M, true>(acc, t, T + (size_t)slot * TS, twq);
-                }
-                if (fp.energy) {  // all lanes take part in the shuffles
-#pragma unroll
-                    for (int off = R1 / 2; off > 0; off >>= 1) en += __shfl_xor_sync(0xffffffffu, en, off);
-                    if (act && t == 0) fp.energy[((size_t)gi * L + l) * Mh + k] = (float)(k == 0 ? en : R(2) * en);
+                    Y[(size_t)i * TS + j] = C{ar, ai};
                 }
                 __syncthreads();
-                if (act) {
-                    C out[CB][R1];
-                    fft_step_b<M, true>(out, t, T + (size_t)slot * TS);
-                    C *dst = fp.w2 + (((size_t)gi * L + l) * Mh + k) * M;
-#pragma unroll
-                    for (int c = 0; c < CB; ++c)
-#pragma unroll
-                        for (int k1 = 0; k1 < R1; ++k1) dst[t + c * R1 + R2 * k1] = out[c][k1];
+                if (fp.energy)  // Parseval partial sums, one warp per (group, layer)
+                    for (int i = warp; i < nact; i += NTH / 32) {
+                        const int task = base + i, gi = task / L, l = task - gi * L;
+                        R e = 0;
+                        for (int j = lane; j < M; j += 32) {
+                            const C v = Y[(size_t)i * TS + j];
+                            e += v.x * v.x + v.y * v.y;
+                        }
+                        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+                        if (lane == 0) fp.energy[((size_t)gi * L + l) * Mh + k] = (float)(k == 0 ? e : R(2) * e);
+                    }
+                fft_core<M>(Y, nact, 1, twq);
+                for (int idx = tid; idx < (nact << LOGM); idx += NTH) {
+                    const int i = idx >> LOGM, p = idx & (M - 1);
+                    const int task = base + i, gi = task / L, l = task - gi * L;
+                    fp.w2[((((size_t)gi * L + l) * Mh + k) << LOGM) + p] = Y[(size_t)i * TS + p];
                 }
                 __syncthreads();
             }
             // next column of this CTA: bring its B block in while the rest runs
-            if (fp.stage_b && k + nb < Mh && tid == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                const C *src = fp.B + (size_t)(k + nb) * colB;
-                mbar_expect_tx(&mbar, colB_bytes);
-                for (unsigned off = 0; off < colB_bytes; off += 32768u)
-                    tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off,
-                                min(32768u, colB_bytes - off), &mbar);
+            if (fp.stage_b && k + nb < Mh) {
+                if (tid == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    const C *src = fp.B + (size_t)(k + nb) * colB;
+                    mbar_expect_tx(&mbar, colB_bytes);
+                    for (unsigned off = 0; off < colB_bytes; off += 32768u)
+                        tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off,
+                                    min(32768u, colB_bytes - off), &mbar);
+                }
+                tma_pending = true;
             }
-            if (fp.stage_b && k + nb < Mh) tma_pending = true;
         }
     }
     if (stamp) {
         __syncthreads();
         if (tid == 0) stamp[6] = gtimer();
     }
-    if (!grid_sync_bounded(fp.bar, fp.status, fp.timeout_ns, &bar_flag)) {
+    if (!grid_sync_bounded(fp.bar, epoch_s, 1, fp.status, fp.timeout_ns, &bar_flag)) {
         drain();
         return;
     }
     if (stamp && tid == 0) stamp[7] = gtimer();
+    if (b == 0 && tid == 0) {  // every CTA has read this launch's epoch: open the next one
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(fp.bar + 1), "l"(epoch_s + 1ull) : "memory");
+    }
 
     // ---- phase 3: (layer, row tile) ----------------------------------------------
     {
@@ -481,14 +456,13 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
         const int st0 = fp.st3[0], st1 = fp.st3[1];
         C *stg0 = (C *)(tfw + M);                               // [Mh][st0]
         C *stg1 = stg0 + (size_t)Mh * st0;                      // [Mh][st1]
-        C *T = stg1 + (size_t)Mh * st1;                         // [cap3][TS]
-        R *rows0 = (R *)(T + (size_t)fp.cap3 * TS);             // [nsrc3[0]][M] real rows
-        R *rows1 = rows0 + (size_t)fp.nsrc3[0] * M;             // [nsrc3[1]][M]
-        const bool rs0 = fp.grp[0].resample != 0, rs1 = fp.ngroups > 1 && fp.grp[1].resample != 0;
+        C *Z = stg1 + (size_t)Mh * st1;                         // [cap3][TS] row-pair transforms
+        const bool rs0 = fp.grp[0].resample != 0;               // only an LGS group (group 0) is resampled
+        const bool two = fp.ngroups > 1;
         for (int it = b; it < fp.n3; it += nb) {
             const int l = it / fp.tiles3, p0 = (it - l * fp.tiles3) * RT;
             const int nr = min(RT, M - p0);
-            if (fp.any_resample)
+            if (rs0)
                 for (int i = tid; i < M; i += NTH) {
                     ti0[i] = fp.rs_i0[l * M + i];
                     tfw[i] = fp.rs_w[l * M + i];
@@ -496,10 +470,10 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
             __syncthreads();
             const int first0 = rs0 ? ti0[p0] : p0;
             const int nsrc0 = rs0 ? ti0[p0 + nr - 1] + 2 - first0 : nr;
-            const int first1 = rs1 ? ti0[p0] : p0;
-            const int nsrc1 = fp.ngroups > 1 ? (rs1 ? ti0[p0 + nr - 1] + 2 - first1 : nr) : 0;
+            const int nsrc1 = two ? nr : 0;  // the NGS group is never resampled
             const int npair0 = (nsrc0 + 1) >> 1, npair1 = (nsrc1 + 1) >> 1;
-            if (nsrc0 > fp.nsrc3[0] || nsrc1 > fp.nsrc3[1]) {  // sized on the host for every tile; never expected
+            const int ntot = npair0 + npair1;
+            if (nsrc0 > fp.nsrc3[0] || nsrc1 > fp.nsrc3[1] || ntot > fp.cap3) {  // sized on the host; never expected
                 if (tid == 0) atomicExch(fp.status, (int)SAFR_ERR_DEVICE);
                 continue;
             }
@@ -508,67 +482,43 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 const C *src0 = fp.w2 + (size_t)l * Mh * M;
                 for (int idx = tid; idx < Mh * nsrc0; idx += NTH) {
                     const int k = idx / nsrc0, s = idx - k * nsrc0;
-                    stg0[k * st0 + s] = __ldcg(src0 + (size_t)k * M + ((first0 + s) & (M - 1)));
+                    stg0[k * st0 + s] = __ldcg(src0 + ((size_t)k << LOGM) + ((first0 + s) & (M - 1)));
                 }
                 const C *src1 = fp.w2 + ((size_t)L + l) * Mh * M;
                 for (int idx = tid; idx < Mh * nsrc1; idx += NTH) {
                     const int k = idx / nsrc1, s = idx - k * nsrc1;
-                    stg1[k * st1 + s] = __ldcg(src1 + (size_t)k * M + ((first1 + s) & (M - 1)));
+                    stg1[k * st1 + s] = __ldcg(src1 + ((size_t)k << LOGM) + p0 + s);
                 }
             }
             __syncthreads();
             if (stamp && tid == 0 && it == b) stamp[8] = gtimer();
-            // complex-to-real transforms of row pairs, both groups in one batch
-            const int ntot = npair0 + npair1;
-            for (int base = 0; base < ntot; base += fp.cap3) {
-                const int task = base + slot;
-                const bool act = slot < fp.cap3 && task < ntot;
-                const bool g1 = act && task >= npair0;
-                const int i = act ? (g1 ? task - npair0 : task) : 0;
-                const int nsg = g1 ? nsrc1 : nsrc0;
-                const bool hasb = act && 2 * i + 1 < nsg;
-                if (act) {
-                    const C *sg = g1 ? stg1 : stg0;
-                    const int st = g1 ? st1 : st0;
-                    C v[R2];
-#pragma unroll
-                    for (int n2 = 0; n2 < R2; ++n2) {
-                        const int k = t + R1 * n2;
-                        C z = C{0, 0};
-                        if (k < Mh) {
-                            C x1 = sg[k * st + 2 * i];
-                            C x2 = hasb ? sg[k * st + 2 * i + 1] : C{0, 0};
-                            if (k == 0) {
-                                x1.y = 0;
-                                x2.y = 0;
-                            }
-                            z = C{x1.x - x2.y, x1.y + x2.x};
-                        } else if (k > Mh) {
-                            const int kk = M - k;
-                            const C x1 = sg[kk * st + 2 * i];
-                            const C x2 = hasb ? sg[kk * st + 2 * i + 1] : C{0, 0};
-                            z = C{x1.x + x2.y, x2.x - x1.y};
-                        }
-                        v[n2] = z;
+            // Z[k] = X1[k] + i X2[k] over the full length M from the stored half spectra of a row pair
+            for (int idx = tid; idx < (ntot << LOGM); idx += NTH) {
+                const int task = idx >> LOGM, k = idx & (M - 1);
+                const bool g1 = task >= npair0;
+                const int i = g1 ? task - npair0 : task;
+                const C *sg = g1 ? stg1 : stg0;
+                const int st = g1 ? st1 : st0;
+                const bool hasb = 2 * i + 1 < (g1 ? nsrc1 : nsrc0);
+                C z = C{0, 0};
+                if (k < Mh) {
+                    C x1 = sg[k * st + 2 * i];
+                    C x2 = hasb ? sg[k * st + 2 * i + 1] : C{0, 0};
+                    if (k == 0) {
+                        x1.y = 0;
+                        x2.y = 0;
                     }
-                    fft_step_a<M, true>(v, t, T + (size_t)slot * TS, twq);
+                    z = C{x1.x - x2.y, x1.y + x2.x};
+                } else if (k > Mh) {
+                    const int kk = M - k;
+                    const C x1 = sg[kk * st + 2 * i];
+                    const C x2 = hasb ? sg[kk * st + 2 * i + 1] : C{0, 0};
+                    z = C{x1.x + x2.y, x2.x - x1.y};
                 }
-                __syncthreads();
-                if (act) {
-                    C out[CB][R1];
-                    fft_step_b<M, true>(out, t, T + (size_t)slot * TS);
-                    R *ra = (g1 ? rows1 : rows0) + (size_t)(2 * i) * M;
-#pragma unroll
-                    for (int c = 0; c < CB; ++c)
-#pragma unroll
-                        for (int k1 = 0; k1 < R1; ++k1) {
-                            const int q = t + c * R1 + R2 * k1;
-                            ra[q] = out[c][k1].x;
-                            if (hasb) ra[M + q] = out[c][k1].y;
-                        }
-                }
-                __syncthreads();
+                Z[(size_t)task * TS + k] = z;
             }
+            __syncthreads();
+            fft_core<M>(Z, ntot, 1, twq);
             if (stamp && tid == 0 && it == b) stamp[9] = gtimer();
             R inv_scale = R(1);
             if (fp.out_scales) {
@@ -582,21 +532,29 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 inv_scale = (R)(1.0 / sc);
                 if (p0 == 0 && tid == 0) fp.out_scales[l] = (float)sc;
             }
+            // source row s of group 0 is Z[s / 2] (real part for even s, imaginary for odd)
             const R f = fp.inv_M2 * inv_scale;
             TOUT *outp = (TOUT *)fp.out + ((size_t)l * M + p0) * M;
             for (int idx = tid; idx < nr * M; idx += NTH) {
-                const int r = idx / M, q = idx & (M - 1);
-                R v = 0;
-                if (rs0 || rs1) {  // bilinear weights of output (p0 + r, q) in the LGS layer grid
+                const int r = idx >> LOGM, q = idx & (M - 1);
+                R v;
+                if (rs0) {  // bilinear in the LGS layer grid (pitch c_l delta)
                     const R fu = tfw[p0 + r], fv = tfw[q];
                     const int j0u = ti0[q];
                     const int ja = j0u & (M - 1), jb = (j0u + 1) & (M - 1);
-                    const R *r0 = (rs0 ? rows0 : rows1) + (size_t)(ti0[p0 + r] - (rs0 ? first0 : first1)) * M;
-                    const R *r1 = r0 + M;
-                    v += (R(1) - fu) * ((R(1) - fv) * r0[ja] + fv * r0[jb]) + fu * ((R(1) - fv) * r1[ja] + fv * r1[jb]);
+                    const int s0 = ti0[p0 + r] - first0, s1 = s0 + 1;
+                    const C *za = Z + (size_t)(s0 >> 1) * TS, *zb = Z + (size_t)(s1 >> 1) * TS;
+                    const R a0 = (s0 & 1) ? za[ja].y : za[ja].x, a1 = (s0 & 1) ? za[jb].y : za[jb].x;
+                    const R b0v = (s1 & 1) ? zb[ja].y : zb[ja].x, b1v = (s1 & 1) ? zb[jb].y : zb[jb].x;
+                    v = (R(1) - fu) * ((R(1) - fv) * a0 + fv * a1) + fu * ((R(1) - fv) * b0v + fv * b1v);
+                } else {
+                    const C zz = Z[(size_t)(r >> 1) * TS + q];
+                    v = (r & 1) ? zz.y : zz.x;
                 }
-                if (!rs0) v += rows0[(size_t)r * M + q];
-                if (fp.ngroups > 1 && !rs1) v += rows1[(size_t)r * M + q];
+                if (two) {  // the NGS group's rows follow group 0's pairs
+                    const C zz = Z[(size_t)(npair0 + (r >> 1)) * TS + q];
+                    v += (r & 1) ? zz.y : zz.x;
+                }
                 if constexpr (std::is_same<TOUT, double>::value)
                     store_out_d(outp + idx, (double)(v * f));
                 else
@@ -632,9 +590,9 @@ struct Frame2Host {
         // phase 1 / 2 scratch, sized for the transforms actually in flight
         const int n1 = G * ((P + 1) / 2);
         const int cap1 = std::min(SLOTS, (n1 + nb - 1) / nb);
-        const int cap2 = std::min(SLOTS, std::max(G, pl->ngroups * L));
-        const size_t s1 = (size_t)cap1 * S::TS * cs + (size_t)cap1 * M * cs;
-        const size_t s2 = (size_t)G * M * cs + (size_t)cap2 * S::TS * cs;
+        const int cap2 = std::min(SLOTS, pl->ngroups * L);
+        const size_t s1 = (size_t)cap1 * S::TS * cs;
+        const size_t s2 = (size_t)G * S::TS * cs + (size_t)cap2 * S::TS * cs;
         const size_t s12 = al(std::max(s1, s2));
         const size_t colB = (size_t)pl->sumLG * M * cs;
         if (G > 32) return false;
@@ -660,9 +618,9 @@ struct Frame2Host {
             }
             size_t s3 = (size_t)M * (4 + rs);
             for (int gi = 0; gi < pl->ngroups; ++gi) s3 += (size_t)Mh * odd_at_least(nsm_[gi]) * cs;
-            const int cap3 = std::min(SLOTS, (nsm_[0] + nsm_[1]) / 2);
+            const int cap3 = (nsm_[0] + nsm_[1]) / 2;  // every row pair of a tile in one batch
+            if (cap3 > SLOTS) continue;
             s3 += (size_t)cap3 * S::TS * cs;
-            for (int gi = 0; gi < pl->ngroups; ++gi) s3 += (size_t)nsm_[gi] * M * rs;
             s3 = al(s3);
             const long long items = (long long)L * ((M + rt - 1) / rt);
             // largest tile that fits and still gives every CTA an item

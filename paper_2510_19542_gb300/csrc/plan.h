@@ -120,7 +120,7 @@ struct safr_plan_s {
     void *d_twq = nullptr;     // [M] four-step twiddles of the persistent kernel
     void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT)
     void *d_pm = nullptr;      // [G][P][2] per-row tip/tilt functionals
-    unsigned *d_bar = nullptr; // grid barrier words
+    unsigned long long *d_bar = nullptr; // grid barrier: arrival count, launch epoch
     unsigned long long *d_stamps = nullptr;  // [grid][SAFR_TRACE_MARKS] timestamps of traced fused frames
     double *d_pre = nullptr;  // shifts, sw, tau of both groups (precompute)
     int *d_status = nullptr;

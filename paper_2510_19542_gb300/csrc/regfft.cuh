@@ -137,4 +137,60 @@ __device__ __forceinline__ void fft_step_b(C (*out)[FftShape<M>::R1], int t, con
     }
 }
 
+// One length-M transform per group of R1 threads ("slot"), in place on
+// shared memory: buf + slot * TS holds x[0..M) in natural order on entry and
+// X[0..M) on return.  inv != 0 gives the unnormalised inverse through
+// IDFT(x) = conj(DFT(conj(x))).  Slots >= nact only take part in the block
+// barriers.  Not inlined: every phase of the frame kernel calls this one copy,
+// which keeps the kernel's instruction footprint small.
+template <int M, typename C>
+__device__ __noinline__ void fft_core(C *buf, int nact, int inv, const C *twq)
+{
+    using S = FftShape<M>;
+    const int slot = threadIdx.x / S::R1, t = threadIdx.x % S::R1;
+    const bool act = slot < nact;
+    C *x = buf + (size_t)slot * S::TS;
+    C v[S::R2];
+    if (act) {
+#pragma unroll
+        for (int n2 = 0; n2 < S::R2; ++n2) {
+            v[n2] = x[t + S::R1 * n2];
+            if (inv) v[n2].y = -v[n2].y;
+        }
+    }
+    __syncthreads();
+    if (act) {
+        dft_reg<S::R2, false>(v);
+#pragma unroll
+        for (int k2 = 0; k2 < S::R2; ++k2) {
+            C y = v[k2];
+            if (k2 > 0) y = c_mul(y, twq[k2 * S::R1 + t]);
+            x[k2 * (S::R1 + 1) + t] = y;
+        }
+    }
+    __syncthreads();
+    C out[S::CB][S::R1];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < S::CB; ++c) {
+            const int k2 = t + c * S::R1;
+#pragma unroll
+            for (int n1 = 0; n1 < S::R1; ++n1) out[c][n1] = x[k2 * (S::R1 + 1) + n1];
+            dft_reg<S::R1, false>(out[c]);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < S::CB; ++c)
+#pragma unroll
+            for (int k1 = 0; k1 < S::R1; ++k1) {
+                C o = out[c][k1];
+                if (inv) o.y = -o.y;
+                x[t + c * S::R1 + S::R2 * k1] = o;
+            }
+    }
+    __syncthreads();
+}
+
 }  // namespace safr
