@@ -52,6 +52,17 @@ def parse():
     return ap.parse_args()
 
 
+def csrc_sha256() -> str:
+    """sha256 over the library sources (file name and bytes, sorted by name)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2510_19542_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        with open(os.path.join(d, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()
+
+
 def config_block(g):
     return {"workload": WORKLOAD, "grid": g["M"], "pupil": g["P"], "lgs": int(np.sum(g["kind"] == 1)),
             "ngs": int(np.sum(g["kind"] == 0)), "layers": len(g["h"]), "batch": 1,
@@ -312,8 +323,11 @@ def run_safr(args):
         traffic = None
         try:
             with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-                traffic = json.load(f).get(WORKLOAD, {}).get(kname)
-        except (OSError, ValueError):
+                rec = json.load(f).get(WORKLOAD, {}).get(kname)
+            # counters taken on other kernel sources say nothing about this build
+            if rec and rec.get("csrc_sha256") == csrc_sha256():
+                traffic = rec["traffic_bytes"]
+        except (OSError, ValueError, KeyError):
             traffic = None
         lat_sorted = sorted(lat)
         value = world * args.steps / (total_ms * 1e-3)
