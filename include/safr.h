@@ -239,6 +239,49 @@ int safr_get_path(safr_plan_t plan);
  */
 safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s);
 
+/*
+ * No counterpart in the paper: a deployment form of safr_reconstruct for
+ * callers that cannot call cudaMalloc.  Examples are a hard-real-time
+ * control thread (an allocation may synchronise the device and has no
+ * latency bound), a plugin inside a host framework that hands out all device
+ * memory from its own pool, or software whose rules forbid dynamic allocation
+ * after start-up.  A plan allocates B, its tables and its workspaces, so such
+ * callers cannot create one.  This entry point needs no plan and allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * It runs the FP32 persistent frame kernel for ONE star group with native
+ * output: all NGS, or all LGS with layers at pitch c_l*delta.  There is no
+ * removeTT, no resample and no second group.  The caller owns every buffer:
+ *   d_B          [M/2][L*G][M] float2 (16-byte aligned): B_lg at frequency
+ *                (j, k) in row l*G + g of column block k, for k < M/2 (the
+ *                same values and order that safr_copy_B returns for the
+ *                group, rounded to FP32);
+ *   d_wavefronts [G][P][P] float (16-byte aligned);
+ *   d_layers     [L][M][M] float (16-byte aligned), sampled at pitch c_l*delta;
+ *   d_status     one int (device memory), which the caller sets to 0.  A
+ *                bounded device-side wait that gives up writes a non-zero
+ *                safr_status (SAFR_ERR_TIMEOUT) there.  It is never cleared.
+ * The kernel's scratch is a file-scope device array of
+ * SAFR_NOALLOC_SCRATCH_BYTES: the grid-barrier counters, the twiddle table,
+ * the row spectra (G*(M/2)*P complex) and the layer spectra (L*(M/2)*M
+ * complex), each rounded up to 256 bytes.  A size that does not fit returns
+ * SAFR_ERR_UNSUPPORTED_SIZE, before anything is launched.  So does a shape
+ * the kernel cannot hold.  Every GPU that loads the library holds the array
+ * until the process exits.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  Every call on a device shares the one array,
+ * and each call re-initialises the parts that must start from zero.  Calls
+ * that overlap on the GPU (other streams, or other threads) race on it and
+ * give wrong layers.  Asynchronous on `stream`; argument errors are returned
+ * synchronously with nothing launched.
+ */
+#define SAFR_NOALLOC_SCRATCH_BYTES (8u << 20) /* 8 MiB */
+safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, int L, int G, const void *d_B,
+                                     const float *d_wavefronts, float *d_layers, int *d_status,
+                                     cudaStream_t stream);
+
 /* Free every device and host resource of the plan (synchronises its device). */
 safr_status safr_destroy(safr_plan_t plan);
 

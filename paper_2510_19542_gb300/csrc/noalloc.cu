@@ -1,0 +1,198 @@
+// safr_reconstruct_noalloc: the FP32 persistent frame kernel run without any
+// device allocation.  The paper has no counterpart; this is a deployment form
+// of the same reconstruction.
+//
+// Some callers cannot call cudaMalloc: a hard-real-time control thread (an
+// allocation may synchronise the device and has no latency bound), a plugin
+// inside a host framework that hands out all device memory from its own pool,
+// or software whose rules forbid dynamic allocation after start-up.  A plan
+// (safr_plan_create) allocates B, its tables and its workspaces, so those
+// callers cannot use one.  Here the caller passes every input (the wavefronts
+// and B) and every output (the layers and a status word) in memory it owns.
+// The kernel's scratch (the row and layer spectra between its phases, its
+// twiddle table and its grid-barrier counters) lives in the file-scope
+// device array below.  That array is part of the library image, so every GPU
+// that loads the library holds it until the process exits.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "frame_impl.cuh"
+#include "plan.h"
+#include "safr.h"
+
+namespace safr {
+bool frame2_configure_f32(safr_plan_s *pl, int nsm);
+void *frame2_kernel_f32(int M);
+}  // namespace safr
+
+namespace {
+
+static_assert(SAFR_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must be a multiple of 256 bytes");
+
+// The shared scratch of every safr_reconstruct_noalloc call on a device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SAFR_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mutex;
+void *g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Twiddles W_M^(n1 k2) of the four-step FFT, laid out [k2][n1] (R1 = 2^floor(log2(M)/2)),
+// from FP64 sincospi, and the grid-barrier counters cleared for this call.
+__global__ void k_noalloc_prepare(float2 *twq, int M, int R1, unsigned long long *bar)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < M) {
+        const int k2 = i / R1, n1 = i - k2 * R1;
+        const long long e = ((long long)n1 * k2) % M;
+        double s, c;
+        sincospi(2.0 * (double)e / (double)M, &s, &c);
+        twq[i] = make_float2((float)c, (float)-s);
+    }
+    if (i == 0) {
+        bar[0] = 0ull;
+        bar[1] = 0ull;
+    }
+}
+
+bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+}  // namespace
+
+extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, int L, int G, const void *d_B,
+                                                const float *d_wavefronts, float *d_layers, int *d_status,
+                                                cudaStream_t stream)
+{
+    if (M < 8 || M > SAFR_MAX_M || (M & (M - 1))) return SAFR_ERR_UNSUPPORTED_SIZE;
+    if (P < 1 || P > M || L < 1 || G < 1) return SAFR_ERR_INVALID_ARG;
+    if (L > SAFR_MAX_L || G > SAFR_MAX_GROUP_G) return SAFR_ERR_UNSUPPORTED_SIZE;
+    if (!d_B || !d_wavefronts || !d_layers || !d_status) return SAFR_ERR_INVALID_ARG;
+    if (!aligned(d_B, 16) || !aligned(d_wavefronts, 16) || !aligned(d_layers, 16) || !aligned(d_status, 4))
+        return SAFR_ERR_MISALIGNED;
+    const int Mh = M / 2;
+    // scratch carve-up: barrier counters | twiddles | row spectra w1 | layer spectra w2
+    const size_t off_twq = 256;
+    const size_t off_w1 = off_twq + align256((size_t)M * sizeof(float2));
+    const size_t off_w2 = off_w1 + align256((size_t)G * Mh * P * sizeof(float2));
+    const size_t need = off_w2 + align256((size_t)L * Mh * M * sizeof(float2));
+    if (need > (size_t)SAFR_NOALLOC_SCRATCH_BYTES) return SAFR_ERR_UNSUPPORTED_SIZE;
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device < 0 || cuda_device >= ndev ||
+        cuda_device >= kMaxDevices) {
+        cudaGetLastError();
+        return SAFR_ERR_CUDA;
+    }
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return SAFR_ERR_CUDA;
+    if (prev != cuda_device && cudaSetDevice(cuda_device) != cudaSuccess) return SAFR_ERR_CUDA;
+    struct Restore {
+        int dev, prev;
+        ~Restore()
+        {
+            if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+        }
+    } restore{cuda_device, prev};
+
+    // set-up, once per device with that device current: the device address of the scratch array
+    unsigned char *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        if (!g_scratch_dev[cuda_device]) {
+            void *ptr = nullptr;
+            if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+                cudaGetLastError();
+                return SAFR_ERR_CUDA;
+            }
+            g_scratch_dev[cuda_device] = ptr;
+        }
+        scratch = (unsigned char *)g_scratch_dev[cuda_device];
+    }
+
+    // launch shape of the persistent kernel for one star group (plan on the stack: no heap use)
+    int nsm = 0, coop = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, cuda_device) != cudaSuccess || !coop) {
+        cudaGetLastError();
+        return SAFR_ERR_CUDA;
+    }
+    safr_plan_s pl;
+    pl.device = cuda_device;
+    pl.M = M;
+    pl.P = P;
+    pl.L = L;
+    pl.G = G;
+    pl.Mh = Mh;
+    pl.o = (M - P) / 2;
+    pl.precision = SAFR_FP32;
+    pl.ngroups = 1;
+    pl.grp[0].G = G;
+    pl.grp[0].b_row0 = 0;
+    pl.grp[0].resample = false;
+    pl.sumLG = L * G;
+    if (!safr::frame2_configure_f32(&pl, nsm)) {
+        cudaGetLastError();
+        return SAFR_ERR_UNSUPPORTED_SIZE;
+    }
+    void *kernel = safr::frame2_kernel_f32(M);
+    if (!kernel) return SAFR_ERR_UNSUPPORTED_SIZE;
+
+    using C = float2;
+    safr::Frame2Params<float> fp;
+    std::memset(&fp, 0, sizeof(fp));
+    fp.P = P;
+    fp.L = L;
+    fp.G = G;
+    fp.o = pl.o;
+    fp.ngroups = 1;
+    fp.sumLG = L * G;
+    fp.npr = (P + 1) / 2;
+    fp.n1 = G * fp.npr;
+    fp.ntask2 = L;
+    fp.rt3 = pl.f2_rt3;
+    fp.cap3 = pl.f2_cap3;
+    fp.tiles3 = pl.f2_tiles3;
+    fp.n3 = pl.f2_n3;
+    for (int gi = 0; gi < 2; ++gi) {
+        fp.st3[gi] = pl.f2_st3[gi];
+        fp.nsrc3[gi] = pl.f2_nsrc3[gi];
+    }
+    fp.any_tt = 0;
+    fp.any_resample = 0;
+    fp.stage_b = pl.f2_stage_b;
+    fp.skip_cta = -1;
+    fp.timeout_ns = 1000000000ull;
+    fp.inv_M2 = (float)(1.0 / ((double)M * M));
+    fp.off_b = pl.f2_off_b;
+    fp.off_s12 = pl.f2_off_s12;
+    fp.off_s3 = pl.f2_off_s3;
+    fp.in = d_wavefronts;
+    fp.out = d_layers;
+    fp.B = (const C *)d_B;
+    fp.w1 = (C *)(scratch + off_w1);
+    fp.w2 = (C *)(scratch + off_w2);
+    fp.twq = (const C *)(scratch + off_twq);
+    fp.bar = (unsigned long long *)scratch;
+    fp.status = d_status;
+    fp.grp[0].G = G;
+    fp.grp[0].b_row0 = 0;
+    fp.grp[0].resample = 0;
+    for (int g = 0; g < G; ++g) fp.grp[0].star[g] = g;
+
+    int logM = 0;
+    while ((1 << logM) < M) ++logM;
+    const int R1 = 1 << (logM / 2);
+    k_noalloc_prepare<<<(M + 255) / 256, 256, 0, stream>>>((float2 *)(scratch + off_twq), M, R1,
+                                                             (unsigned long long *)scratch);
+    if (cudaGetLastError() != cudaSuccess) return SAFR_ERR_CUDA;
+    void *args[] = {&fp};
+    if (cudaLaunchCooperativeKernel(kernel, dim3(pl.f2_grid), dim3(512), args, pl.f2_smem, stream) != cudaSuccess) {
+        cudaGetLastError();
+        return SAFR_ERR_CUDA;
+    }
+    return SAFR_OK;
+}

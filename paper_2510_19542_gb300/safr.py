@@ -35,7 +35,8 @@ _PRECISION = {"fp32": SAFR_FP32, "fp16": SAFR_FP16_STORAGE, "fp64": SAFR_FP64}
 _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_reconstruct_host",
             "safr_get_status", "safr_get_plan_info", "safr_copy_B", "safr_trace", "safr_trace_read",
             "safr_launches_per_frame", "safr_trace_phases", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
-            "safr_destroy", "safr_status_string"]
+            "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc"]
+SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class SafrError(RuntimeError):
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = True):
     lib.safr_get_path.argtypes = [vp]
     lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
     lib.safr_destroy.argtypes = [vp]
+    lib.safr_reconstruct_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     lib.safr_status_string.argtypes = [C.c_int]
     lib.safr_status_string.restype = C.c_char_p
     for name in _EXPORTS:
@@ -241,6 +243,15 @@ def safr_get_path(plan: int) -> int:
 
 def safr_debug_skip_barrier(plan: int, cta: int, timeout_s: float = 0.0):
     _check(load().safr_debug_skip_barrier(plan, int(cta), float(timeout_s)), "safr_debug_skip_barrier")
+
+
+def safr_reconstruct_noalloc(cuda_device: int, M: int, P: int, L: int, G: int, B, wavefronts, layers, status,
+                             stream=None):
+    """Plan-free FP32 frame of one star group with caller-owned buffers and no
+    device allocation (scratch in the library's static device array)."""
+    _check(load().safr_reconstruct_noalloc(int(cuda_device), int(M), int(P), int(L), int(G), _ptr(B),
+                                           _ptr(wavefronts), _ptr(layers), _ptr(status), _stream(stream)),
+           "safr_reconstruct_noalloc")
 
 
 def safr_destroy(plan: int):
