@@ -207,11 +207,21 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
 /*
  * Inside the last traced SAFR_PATH_FUSED frame, in microseconds from the
  * first CTA's start (read from %globaltimer), the time the last CTA reached
- * each of 11 marks: 0 start, 1 prologue done, 2 first phase-1 transforms done,
- * 3 phase 1 done, 4 out of grid barrier 1, 5 first column's forward
- * transforms done, 6 phase 2 done, 7 out of grid barrier 2, 8 first phase-3
- * tile staged, 9 its transforms done, 10 phase 3 done (0 for a mark no CTA
- * reached).  Writes up to `n` values; *n_out = 11.  SAFR_ERR_INVALID_ARG if
+ * each of 23 marks (0 for a mark no CTA reached):
+ *    0 start                          12 phase 2: first inverse transforms done
+ *    1 prologue issued                13 phase 2: layer spectra stored
+ *    2 phase 1: frame data in         14 phase 2 done
+ *    3 phase 1: B copy issued         15 grid barrier 2: arrival
+ *    4 phase 1: first row transforms  16 grid barrier 2: released
+ *    5 phase 1 done                   17 phase 3: resample tables ready
+ *    6 grid barrier 1: arrival        18 phase 3: source rows staged
+ *    7 grid barrier 1: released       19 phase 3: row transforms done
+ *    8 phase 2: star transforms done  20 phase 3: block synchronised
+ *    9 phase 2: spectra synchronised  21 phase 3: first item stored
+ *   10 phase 2: B block landed        22 phase 3 done
+ *   11 phase 2: first apply done
+ * (marks 2-4, 8-13 and 17-21 are taken on the CTA's first batch, column or
+ * item).  Writes up to `n` values; *n_out = 23.  SAFR_ERR_INVALID_ARG if
  * there is no traced persistent-kernel frame.
  */
 safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out);
@@ -253,9 +263,12 @@ safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s)
  * output: all NGS, or all LGS with layers at pitch c_l*delta.  There is no
  * removeTT, no resample and no second group.  The caller owns every buffer:
  *   d_B          [M/2][L*G][M] float2 (16-byte aligned): B_lg at frequency
- *                (j, k) in row l*G + g of column block k, for k < M/2 (the
- *                same values and order that safr_copy_B returns for the
- *                group, rounded to FP32);
+ *                (j, k) in row l*G + g of column block k, for k < M/2, at
+ *                position pos(j) of the row: the values safr_copy_B returns
+ *                for the group, rounded to FP32, in the frame kernel's
+ *                frequency order.  With LW = min(M, 32), R = M / LW and
+ *                brev(m) the reversal of the log2(LW) bits of m:
+ *                pos(j) = (j mod R) * LW + brev(j div R);
  *   d_wavefronts [G][P][P] float (16-byte aligned);
  *   d_layers     [L][M][M] float (16-byte aligned), sampled at pitch c_l*delta;
  *   d_status     one int (device memory), which the caller sets to 0.  A

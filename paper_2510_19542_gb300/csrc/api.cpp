@@ -11,6 +11,7 @@
 #include <new>
 #include <vector>
 
+#include "freqorder.h"
 #include "plan.h"
 #include "safr.h"
 
@@ -335,32 +336,38 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
             xs.assign(half, 0.0);
             ys.assign(half, 0.0);
         }
+        // stored with j in the persistent kernel's warp-FFT order: entry [k][pos] is frequency (j(pos), k)
+        auto src = [&](size_t i) {
+            const size_t k = i / M, pos = i % M;
+            return k * M + (size_t)safr::wfft_j_of_pos((int)pos, M);
+        };
         if (p->precision == SAFR_FP64) {
             std::vector<double2> h(2 * half);
             for (size_t i = 0; i < half; ++i) {
-                h[i] = make_double2(xs[i].real(), xs[i].imag());
-                h[half + i] = make_double2(ys[i].real(), ys[i].imag());
+                h[i] = make_double2(xs[src(i)].real(), xs[src(i)].imag());
+                h[half + i] = make_double2(ys[src(i)].real(), ys[src(i)].imag());
             }
             SAFR_TRY(upload((double2 **)&p->d_xy_hat, h));
         } else {
             std::vector<float2> h(2 * half);
             for (size_t i = 0; i < half; ++i) {
-                h[i] = make_float2((float)xs[i].real(), (float)xs[i].imag());
-                h[half + i] = make_float2((float)ys[i].real(), (float)ys[i].imag());
+                h[i] = make_float2((float)xs[src(i)].real(), (float)xs[src(i)].imag());
+                h[half + i] = make_float2((float)ys[src(i)].real(), (float)ys[src(i)].imag());
             }
             SAFR_TRY(upload((float2 **)&p->d_xy_hat, h));
         }
     }
-    {   // four-step twiddles W_M^(n1 k2) of the persistent kernel, from FP64
+    {   // warp-FFT twiddles of the persistent kernel, from FP64
         std::vector<double> tr, ti;
         safr::frame2_twiddles(M, tr, ti);
+        const size_t nt = tr.size();
         if (p->precision == SAFR_FP64) {
-            std::vector<double2> h(M);
-            for (int i = 0; i < M; ++i) h[i] = make_double2(tr[i], ti[i]);
+            std::vector<double2> h(nt);
+            for (size_t i = 0; i < nt; ++i) h[i] = make_double2(tr[i], ti[i]);
             SAFR_TRY(upload((double2 **)&p->d_twq, h));
         } else {
-            std::vector<float2> h(M);
-            for (int i = 0; i < M; ++i) h[i] = make_float2((float)tr[i], (float)ti[i]);
+            std::vector<float2> h(nt);
+            for (size_t i = 0; i < nt; ++i) h[i] = make_float2((float)tr[i], (float)ti[i]);
             SAFR_TRY(upload((float2 **)&p->d_twq, h));
         }
     }
@@ -552,14 +559,17 @@ safr_status safr_copy_B(safr_plan_t plan, int group, double *dst)
             return SAFR_ERR_CUDA;
         double *d = dst + (size_t)k * rows * M * 2;
         for (size_t i = 0; i < rows * M; ++i) {
+            // device storage is in the warp-FFT order along j; hand it back in natural order
+            const size_t row = i / M, pos = i % M;
+            const size_t o = row * M + (size_t)safr::wfft_j_of_pos((int)pos, M);
             if (f64) {
                 const double2 v = ((const double2 *)buf.data())[i];
-                d[2 * i] = v.x;
-                d[2 * i + 1] = v.y;
+                d[2 * o] = v.x;
+                d[2 * o + 1] = v.y;
             } else {
                 const float2 v = ((const float2 *)buf.data())[i];
-                d[2 * i] = v.x;
-                d[2 * i + 1] = v.y;
+                d[2 * o] = v.x;
+                d[2 * o + 1] = v.y;
             }
         }
     }

@@ -2,29 +2,38 @@
 // size M fixed at compile time (instantiated per precision in frame_*.cu).
 //
 // All CTAs are co-resident (cooperative launch, one per SM, 512 threads) and
-// run three phases separated by two grid-wide barriers:
+// run three phases separated by two grid-wide barriers.  Every transform is a
+// warp-level FFT (warpfft.cuh): one group of min(M, 32) lanes per transform,
+// all data in registers, lanes exchanged by shuffles.
 //
-//   prologue  TMA bulk copy of the B block of this CTA's first column k
-//             (all groups, layers and stars; contiguous in memory) into shared
-//             memory, and an L2 bulk prefetch of the B of its later columns, so
-//             the dominant byte stream lands during phase 1;
-//   phase 1   row pairs of the zero-padded wavefronts (Section 2): two real
-//             rows packed into one complex length-M FFT along q, split into
-//             two half spectra -> w1[g][k][p] (k < M/2).  LGS rows of a mixed
-//             plan also contribute their share of the two linear functionals
-//             that give the tip and tilt of the least-squares plane over the
-//             pupil (Algorithm 3, line 3);
-//   phase 2   columns k: FFT along p of every star's column -> d_g(j, k);
+//   prologue  per-lane twiddles and this CTA's later-phase tables are loaded
+//             into registers; B of every column after this CTA's first goes
+//             to L2 by bulk prefetch;
+//   phase 1   one transform per row pair of the zero-padded wavefronts
+//             (Section 2): rows a0, a0 + 1 packed as z = psi_a0 + i psi_a0+1,
+//             forward FFT along q, split into the two half spectra
+//             -> w1[g][k][p] (k < M/2).  LGS rows of a mixed plan also give
+//             their share of the two linear functionals that yield the tip and
+//             tilt of the least-squares plane over the pupil (Algorithm 3,
+//             line 3).  Once the frame data has landed, the CTA's first B
+//             column block (all groups, layers and stars; contiguous) is
+//             copied into shared memory by TMA (cp.async.bulk);
+//   phase 2   column k: one transform per star, FFT along p -> d_g(j, k);
 //             removeTT in the frequency domain, d_g -= b_g X(j,k) + c_g Y(j,k)
-//             with X, Y = DFT2 of x and y on the mask (DFT2 is linear); per
-//             frequency and layer b_l = sum_g B_lg d_g (Algorithm 1, line 5)
-//             straight into the registers of the inverse FFT along j ->
-//             w2[group][l][k][p];
-//   phase 3   (layer, tile of output rows): complex-to-real inverse FFT of
-//             the needed rows (IDFT2, 1/M^2), bilinear resample of LGS layers
-//             from pitch c_l*delta to delta, sum of the groups (Algorithm 3,
-//             line 4), optional FP16 with a power-of-two scale from the layer
-//             energy (Parseval), store.
+//             with X, Y = DFT2 of x and y on the mask (DFT2 is linear); then
+//             one transform per (group, layer): b_l = sum_g B_lg d_g at every
+//             frequency (Algorithm 1, line 5) straight into the registers of
+//             the inverse FFT along j -> w2[group][l][k][p];
+//   phase 3   (layer, tile of output rows): the needed rows of w2 staged in
+//             shared memory, one inverse transform per source row pair
+//             (complex-to-real, IDFT2 with 1/M^2), bilinear resample of LGS
+//             layers from pitch c_l*delta to delta, sum of the groups
+//             (Algorithm 3, line 4), optional FP16 with a power-of-two scale
+//             from the layer energy (Parseval), store.
+//
+// The forward transforms leave the frequency index j in the permuted order
+// of freqorder.h; B, the removeTT spectra and the column spectra are stored
+// in that order, and the inverse transforms take it back to natural order.
 //
 // Every wait is bounded: the grid barriers and the TMA completion waits read
 // %globaltimer and give up after a time limit, recording SAFR_ERR_TIMEOUT in
@@ -43,8 +52,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "freqorder.h"
 #include "plan.h"
-#include "regfft.cuh"
+#include "warpfft.cuh"
 
 namespace safr {
 
@@ -56,7 +66,7 @@ struct Frame2Params {
     int ntask2;                // phase-2 (group, layer) tasks = ngroups * L
     int rt3, tiles3, n3;       // phase-3 rows per item, tiles per layer, items
     int st3[2];                // staged source rows per group (odd stride)
-    int cap3;                  // row-pair transforms in flight in phase 3
+    int cap3;                  // row-pair transforms of one phase-3 item (rows of Zr)
     int nsrc3[2];              // max source rows per group and item
     int any_tt, any_resample;
     int stage_b;               // 1: B column block staged in shared memory by TMA
@@ -64,20 +74,20 @@ struct Frame2Params {
     unsigned long long timeout_ns;
     R inv_M2;
     // shared-memory carve-up (bytes from the dynamic base)
-    unsigned off_b, off_s12, off_s3;
+    unsigned off_rs, off_b, off_d, off_xy, off_s3;
     const void *in;
     const float *in_scales;
     void *out;
     float *out_scales;
-    const C *B;                // [M/2][sumLG][M]
+    const C *B;                // [M/2][sumLG][M], j in the permuted order
     C *w1;                     // [G][M/2][P]
     C *w2;                     // [ngroups][L][M/2][M]
     float *energy;             // [ngroups][L][M/2]
-    const C *twq;              // [R2][R1] W_M^(n1 k2)
+    const C *twq;              // [M + LW] warp-FFT twiddles (WTw layout)
     const int *rs_i0;          // [L][M]
     const R *rs_w;             // [L][M]
     const R *tt_w;             // [2][P][P]
-    const C *xy_hat;           // [2][M/2][M]
+    const C *xy_hat;           // [2][M/2][M], j in the permuted order
     R *pm;                     // [G][P][2]
     unsigned long long *bar;   // [2] arrival count, launch epoch
     unsigned long long *stamps;
@@ -115,6 +125,13 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
         : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (bypassing registers); complete after cp_async_wait_all
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
 {
     unsigned ok;
@@ -149,19 +166,21 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 }
 
 // Grid-wide barrier number `which` (0, 1) of the cooperative launch with epoch
-// `epoch`.  bar[0] counts arrivals over the plan's lifetime: every launch adds
+// `epoch` (read by thread 0; other threads' value is not used).  bar[0] counts arrivals over the plan's lifetime: every launch adds
 // 2 * gridDim.x, so barrier `which` of epoch E is complete when the count
 // reaches (2E + which + 1) * gridDim.x.  Arrival is one release reduction (no
 // round trip); one thread per CTA polls with acquire loads until the count is
 // reached or the time limit passes.  Returns false (SAFR_ERR_TIMEOUT recorded)
 // on a timeout.
 __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsigned long long epoch, int which,
-                                                  int *status, unsigned long long timeout_ns, int *flag)
+                                                  int *status, unsigned long long timeout_ns, int *flag,
+                                                  unsigned long long *arrive_mark)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long target = (2ull * epoch + (unsigned long long)which + 1ull) * gridDim.x;
         asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
+        if (arrive_mark) *arrive_mark = gtimer();
         int ok = 1;
         if (ld_acquire_u64(bar) < target) {
             const unsigned long long t0 = gtimer();
@@ -179,56 +198,113 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsig
     return *flag != 0;
 }
 
+
 template <int M, typename R, typename TIN, typename TOUT>
 __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
 {
     using C = typename Frame2Params<R>::C;
-    using S = FftShape<M>;
-    constexpr int TS = S::TS;
+    using S = WShape<M>;
+    constexpr int LW = S::LW, RR = S::R, LB = S::LB;
     constexpr int Mh = M / 2;
     constexpr int LOGM = S::LOG;
     constexpr int NTH = 512;
-    constexpr int SLOTS = NTH / S::R1;
+    constexpr int NW = NTH / 32;
+    constexpr int UNITS = NW * S::TPW;  // transforms in flight per CTA
+    constexpr int QC = 4;               // per-lane loads in flight in the pupil loops
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int bar_flag;
-    __shared__ unsigned long long epoch_s;
-    __shared__ R tt_b[SAFR_MAX_G], tt_c[SAFR_MAX_G];
     __shared__ R red[32];
+    // kernel-parameter arrays indexed at run time, copied once: indexing the
+    // parameter block with a run-time index would place it in local memory
+    __shared__ int s_star_tt[SAFR_MAX_G];
+    __shared__ GroupDev s_grp[2];
+    __shared__ R s_ttb[SAFR_MAX_G], s_ttc[SAFR_MAX_G];  // tip and tilt of each LGS star (phase 2)
 
     const int P = fp.P, o = fp.o, L = fp.L, G = fp.G;
     const int tid = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
     const int lane = tid & 31, warp = tid >> 5;
+    const int t = lane & (LW - 1);                             // lane within the transform
+    const int unit = warp * S::TPW + (lane >> LB);             // transform slot of this lane
+    const int bt = LB > 0 ? (int)(__brev((unsigned)t) >> (32 - LB)) : 0;  // brev(t)
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < SAFR_MAX_G; ++i)
+            if (lane == (i & 31)) s_star_tt[i] = fp.star_tt[i];
+    } else if (warp == 1) {
+#pragma unroll
+        for (int gi = 0; gi < 2; ++gi) {
+            if (lane == 0) {
+                s_grp[gi].G = fp.grp[gi].G;
+                s_grp[gi].b_row0 = fp.grp[gi].b_row0;
+                s_grp[gi].resample = fp.grp[gi].resample;
+            }
+#pragma unroll
+            for (int q = 0; q < SAFR_MAX_GROUP_G; ++q)
+                if (lane == q) s_grp[gi].star[q] = fp.grp[gi].star[q];
+        }
+    }
     unsigned long long *stamp = fp.stamps ? fp.stamps + (size_t)b * SAFR_TRACE_MARKS : nullptr;
-    if (stamp && tid == 0) stamp[0] = gtimer();
-    // epoch of this launch: advanced by CTA 0 once every CTA is past the last barrier
-    if (tid == 0) epoch_s = ld_acquire_u64(fp.bar + 1);
+#define SAFR_MARK(n, cond)                                   \
+    do {                                                     \
+        if (stamp && tid == 0 && (cond)) stamp[n] = gtimer(); \
+    } while (0)
+    SAFR_MARK(0, true);
+    // epoch of this launch (thread 0 only; first used at grid barrier 1).  The
+    // previous launch wrote it; stream order makes that write visible, so a plain
+    // load does (an acquire load would stall thread 0 here until it lands).
+    const unsigned long long epoch = tid == 0 ? __ldcg(fp.bar + 1) : 0ull;
 
-    C *twq = (C *)smem;                      // [M]
-    C *Bs = (C *)(smem + fp.off_b);          // staged B column block
-    unsigned char *s12 = smem + fp.off_s12;  // phase 1 / 2 scratch
-    unsigned char *s3 = smem + fp.off_s3;    // phase 3 scratch (may overlap Bs)
+    C *Bs = (C *)(smem + fp.off_b);   // staged B column block
+    C *Dp = (C *)(smem + fp.off_d);   // [G][M] column spectra (permuted j)
+    C *xys = (C *)(smem + fp.off_xy); // [2][M] removeTT spectra of this CTA's first column (permuted j)
+    unsigned char *s3 = smem + fp.off_s3;
     const size_t colB = (size_t)fp.sumLG * M;  // complex per B column block
     const unsigned colB_bytes = (unsigned)(colB * sizeof(C));
+    const bool rs0 = fp.grp[0].resample != 0;  // only an LGS group (group 0) is resampled
 
     // ---- prologue ------------------------------------------------------------
+    // Each phase issues all of its global loads before it consumes any of
+    // them.  The per-lane twiddles and the values this CTA needs in later
+    // phases are loaded into registers here and land while phase 1 runs.
     unsigned tma_phase = 0;
     bool tma_pending = false;
     if (tid == 0 && fp.stage_b) mbar_init(&mbar, 1);
-    // B of the first column is requested once this CTA's phase-1 input has
-    // arrived, so the 20+ MB stream does not queue ahead of those loads
-    auto issue_first_b = [&]() {
-        if (fp.stage_b && b < Mh && !tma_pending) {
-            if (tid == 0) {
-                const C *src = fp.B + (size_t)b * colB;
-                mbar_expect_tx(&mbar, colB_bytes);
-                for (unsigned off = 0; off < colB_bytes; off += 32768u)
-                    tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off,
-                                min(32768u, colB_bytes - off), &mbar);
-            }
-            tma_pending = true;
-        }
+    auto copy_b = [&](int k) {  // thread 0 only
+        const C *src = fp.B + (size_t)k * colB;
+        mbar_expect_tx(&mbar, colB_bytes);
+        for (unsigned off = 0; off < colB_bytes; off += 32768u)
+            tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off, min(32768u, colB_bytes - off),
+                        &mbar);
     };
+    __shared__ C s_w32[32];
+    wtw_fill_w32(s_w32);
+    WTw<M, C> tw;
+    tw.load(fp.twq, s_w32, t);
+    // this CTA's first phase-2 column of the removeTT spectra and its first phase-3
+    // item's resample tables: asynchronous copies into shared memory of their own
+    int *ti0 = (int *)(smem + fp.off_rs);  // [M]
+    R *tfw = (R *)(ti0 + M);               // [M]
+    const bool xy_pre = fp.any_tt && b < Mh;
+    if (xy_pre) {
+        constexpr int CH = M * (int)sizeof(C) / 16;  // 16-byte chunks per row
+        for (int c = tid; c < 2 * CH; c += NTH) {
+            const int row = c / CH, off = c - row * CH;
+            cp_async16((unsigned char *)(xys + row * M) + off * 16,
+                       (const unsigned char *)(fp.xy_hat + ((size_t)(row * Mh + b) << LOGM)) + off * 16);
+        }
+    }
+    const bool rs_pre = rs0 && b < fp.n3;
+    if (rs_pre) {
+        const int l = b / fp.tiles3;
+        constexpr int CI = M * 4 / 16, CW = M * (int)sizeof(R) / 16;
+        for (int c = tid; c < CI + CW; c += NTH) {
+            if (c < CI)
+                cp_async16((unsigned char *)ti0 + c * 16, (const unsigned char *)(fp.rs_i0 + (size_t)l * M) + c * 16);
+            else
+                cp_async16((unsigned char *)tfw + (c - CI) * 16, (const unsigned char *)(fp.rs_w + (size_t)l * M) + (c - CI) * 16);
+        }
+    }
     {   // later columns of this CTA (or every column when B is not staged): into L2
         const int k0 = fp.stage_b ? b + nb : b;
         for (int k = k0; k < Mh; k += nb) {
@@ -237,8 +313,8 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 prefetch_l2(base + off, min(4096u, colB_bytes - off));
         }
     }
-    for (int i = tid; i < M; i += NTH) twq[i] = fp.twq[i];
-    if (stamp && tid == 0) stamp[1] = gtimer();
+    __syncthreads();  // the W_32 table and the parameter copies
+    SAFR_MARK(1, true);
 
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
     auto drain = [&]() {
@@ -248,131 +324,165 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     // ---- phase 1: row pairs ----------------------------------------------------
     {
         const int lo = (int)(((long long)b * fp.n1) / nb), hi = (int)(((long long)(b + 1) * fp.n1) / nb);
-        const int cap1 = min(SLOTS, (fp.n1 + nb - 1) / nb);  // row pairs per batch
-        C *X = (C *)s12;                                      // [cap1][TS]
-        for (int base = lo; base < hi; base += cap1) {
-            const int nact = min(cap1, hi - base);
-            // z[q] = psi[row a0][q - o] + i psi[row a0 + 1][q - o], zero outside the pupil
-            for (int idx = tid; idx < (nact << LOGM); idx += NTH) {
-                const int i = idx >> LOGM, q = idx & (M - 1);
-                const int item = base + i, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
-                const int qq = q - o;
-                R re = 0, im = 0;
-                if (qq >= 0 && qq < P) {
-                    const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
-                    const R sc = fp.in_scales ? (R)fp.in_scales[g] : R(1);
-                    re = load_in<R>(psi + (size_t)a0 * P + qq) * sc;
-                    if (a0 + 1 < P) im = load_in<R>(psi + (size_t)(a0 + 1) * P + qq) * sc;
-                }
-                X[(size_t)i * TS + q] = C{re, im};
-            }
-            __syncthreads();
-            issue_first_b();
-            // per-row shares of the tip/tilt functionals (one warp per row pair)
-            if (fp.any_tt)
-                for (int i = warp; i < nact; i += NTH / 32) {
-                    const int item = base + i, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
-                    if (!fp.star_tt[g]) continue;
-                    const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
-                    R s0b = 0, s0c = 0, s1b = 0, s1c = 0;
-                    for (int q = lane; q < P; q += 32) {
-                        const C v = X[(size_t)i * TS + o + q];
-                        s0b += wb[a0 * P + q] * v.x;
-                        s0c += wc[a0 * P + q] * v.x;
-                        if (a0 + 1 < P) {
-                            s1b += wb[(a0 + 1) * P + q] * v.y;
-                            s1c += wc[(a0 + 1) * P + q] * v.y;
-                        }
-                    }
-                    for (int off = 16; off > 0; off >>= 1) {
-                        s0b += __shfl_xor_sync(0xffffffffu, s0b, off);
-                        s0c += __shfl_xor_sync(0xffffffffu, s0c, off);
-                        s1b += __shfl_xor_sync(0xffffffffu, s1b, off);
-                        s1c += __shfl_xor_sync(0xffffffffu, s1c, off);
-                    }
-                    if (lane == 0) {
-                        R *d = fp.pm + ((size_t)g * P + a0) * 2;
-                        d[0] = s0b;
-                        d[1] = s0c;
-                        if (a0 + 1 < P) {
-                            d[2] = s1b;
-                            d[3] = s1c;
-                        }
+        bool first = true;
+        for (int base = lo; base < hi; base += UNITS) {
+            const int i = base + unit;
+            const bool act = i < hi;
+            const int item = act ? i : lo, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
+            const bool has1 = a0 + 1 < P;
+            const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
+            const R sc = fp.in_scales ? (R)fp.in_scales[g] : R(1);
+            const bool tt = act && fp.any_tt && s_star_tt[g];
+            const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
+            // z[q] = psi[a0][q - o] + i psi[a0 + 1][q - o]: lane t holds q = t + LW r
+            C v[RR];
+            R s0b = 0, s0c = 0, s1b = 0, s1c = 0;
+#pragma unroll
+            for (int r = 0; r < RR; ++r) {
+                const int qq = t + LW * r - o;
+                const bool in = act && qq >= 0 && qq < P;
+                const R x0 = in ? load_in<R>(psi + (size_t)a0 * P + qq) : R(0);
+                const R x1 = in && has1 ? load_in<R>(psi + (size_t)(a0 + 1) * P + qq) : R(0);
+                v[r] = C{x0 * sc, x1 * sc};
+                if (tt && in) {
+                    s0b += wb[a0 * P + qq] * v[r].x;
+                    s0c += wc[a0 * P + qq] * v[r].x;
+                    if (has1) {
+                        s1b += wb[(a0 + 1) * P + qq] * v[r].y;
+                        s1c += wc[(a0 + 1) * P + qq] * v[r].y;
                     }
                 }
-            fft_core<M>(X, nact, 0, twq);
-            if (stamp && tid == 0 && base == lo) stamp[2] = gtimer();
-            // X1 = (Z[k] + conj Z[M-k]) / 2, X2 = (Z[k] - conj Z[M-k]) / 2i, row pair fastest
-            for (int idx = tid; idx < nact * Mh; idx += NTH) {
-                const int k = idx / nact, i = idx - k * nact;
-                const int it2 = base + i, g2 = it2 / fp.npr, b0 = 2 * (it2 - g2 * fp.npr);
-                const C z = X[(size_t)i * TS + k];
-                const C zc = X[(size_t)i * TS + ((M - k) & (M - 1))];
-                C *dst = fp.w1 + ((size_t)g2 * Mh + k) * P + b0;
-                dst[0] = C{R(0.5) * (z.x + zc.x), R(0.5) * (z.y - zc.y)};
-                if (b0 + 1 < P) dst[1] = C{R(0.5) * (z.y + zc.y), R(0.5) * (zc.x - z.x)};
             }
-            __syncthreads();
+            if (fp.any_tt) {  // per-row shares of the tip/tilt functionals
+#pragma unroll
+                for (int off = LW / 2; off > 0; off >>= 1) {
+                    s0b += __shfl_xor_sync(0xffffffffu, s0b, off);
+                    s0c += __shfl_xor_sync(0xffffffffu, s0c, off);
+                    s1b += __shfl_xor_sync(0xffffffffu, s1b, off);
+                    s1c += __shfl_xor_sync(0xffffffffu, s1c, off);
+                }
+                if (tt && t == 0) {
+                    R *d = fp.pm + ((size_t)g * P + a0) * 2;
+                    d[0] = s0b;
+                    d[1] = s0c;
+                    if (has1) {
+                        d[2] = s1b;
+                        d[3] = s1c;
+                    }
+                }
+            }
+            SAFR_MARK(2, first);
+            // the frame data has landed: B streams in behind it
+            if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);
+            SAFR_MARK(3, first);
+            wfft_fwd<M>(v, tw, t);
+            SAFR_MARK(4, first);
+            // Z[k] sits in register k_r of lane t for k = k_r + R brev(t); Z[M - k] in
+            // register R - k_r of lane t ^ (LW - 1) (k_r > 0), or register 0 of lane
+            // brev(LW - brev(t)) (k_r = 0).  Even lanes hold k < M/2.
+            C zc[RR];
+            zc[0] = C{__shfl_sync(0xffffffffu, v[0].x, (int)(__brev((unsigned)((LW - bt) & (LW - 1))) >> (32 - LB)), LW),
+                      __shfl_sync(0xffffffffu, v[0].y, (int)(__brev((unsigned)((LW - bt) & (LW - 1))) >> (32 - LB)), LW)};
+#pragma unroll
+            for (int k = 1; k < RR; ++k) zc[k] = shfl_xor_c(v[RR - k], LW - 1);
+            if (act && (t & 1) == 0) {
+                C *dst = fp.w1 + (size_t)g * Mh * P + a0;
+#pragma unroll
+                for (int k = 0; k < RR; ++k) {
+                    const int kk = k + RR * bt;
+                    const C z = v[k], w = zc[k];
+                    // X1 = (Z[k] + conj Z[M-k]) / 2, X2 = (Z[k] - conj Z[M-k]) / 2i
+                    dst[(size_t)kk * P] = C{R(0.5) * (z.x + w.x), R(0.5) * (z.y - w.y)};
+                    if (has1) dst[(size_t)kk * P + 1] = C{R(0.5) * (z.y + w.y), R(0.5) * (w.x - z.x)};
+                }
+            }
+            first = false;
         }
+        if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);  // a CTA without phase-1 rows
+        if (fp.stage_b && b < Mh) tma_pending = true;
     }
-    issue_first_b();  // CTAs without phase-1 rows
+    cp_async_wait_all();  // this thread's prologue copies (visible to the CTA after the barrier)
     if (b == fp.skip_cta) {  // test hook: every other CTA's first barrier must time out
         drain();
         return;
     }
-    if (stamp) {
-        __syncthreads();
-        if (tid == 0) stamp[3] = gtimer();
-    }
-    if (!grid_sync_bounded(fp.bar, epoch_s, 0, fp.status, fp.timeout_ns, &bar_flag)) {
+    SAFR_MARK(5, true);
+    if (!grid_sync_bounded(fp.bar, epoch, 0, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 6 : nullptr)) {
         drain();
         return;
     }
-    if (stamp && tid == 0) stamp[4] = gtimer();
+    SAFR_MARK(7, true);
 
     // ---- phase 2: columns --------------------------------------------------------
     {
-        for (int g = warp; fp.any_tt && g < G; g += NTH / 32) {
-            R sb = 0, sc = 0;
-            if (fp.star_tt[g])
-                for (int a = lane; a < P; a += 32) {
-                    const R *d = fp.pm + ((size_t)g * P + a) * 2;
-                    sb += __ldcg(d);
-                    sc += __ldcg(d + 1);
-                }
-            for (int off = 16; off > 0; off >>= 1) {
-                sb += __shfl_xor_sync(0xffffffffu, sb, off);
-                sc += __shfl_xor_sync(0xffffffffu, sc, off);
-            }
-            if (lane == 0) {
-                tt_b[g] = sb;
-                tt_c[g] = sc;
-            }
-        }
-        const int cap2 = min(SLOTS, fp.ntask2);
-        C *D = (C *)s12;                  // [G][TS] spectra d_g(j) of the column
-        C *Y = D + (size_t)G * TS;        // [cap2][TS] layer spectra -> inverse transforms
+        bool first_col = true;
         for (int k = b; k < Mh; k += nb) {
-            // every star's column of w1, zero-padded (p contiguous: coalesced)
-            for (int idx = tid; idx < (G << LOGM); idx += NTH) {
-                const int s = idx >> LOGM, p = idx & (M - 1), pp = p - o;
-                D[(size_t)s * TS + p] = (pp >= 0 && pp < P) ? __ldcg(fp.w1 + ((size_t)s * Mh + k) * P + pp) : C{0, 0};
-            }
-            __syncthreads();
-            for (int base = 0; base < G; base += SLOTS) fft_core<M>(D + (size_t)base * TS, min(SLOTS, G - base), 0, twq);
-            if (fp.any_tt) {  // d_g -= b_g X(j, k) + c_g Y(j, k) for the LGS stars
-                for (int idx = tid; idx < (G << LOGM); idx += NTH) {
-                    const int s = idx >> LOGM, j = idx & (M - 1);
-                    if (!fp.star_tt[s]) continue;
-                    const C xh = fp.xy_hat[((size_t)k << LOGM) + j];
-                    const C yh = fp.xy_hat[((size_t)(Mh + k) << LOGM) + j];
-                    C &d = D[(size_t)s * TS + j];
-                    d.x -= tt_b[s] * xh.x + tt_c[s] * yh.x;
-                    d.y -= tt_b[s] * xh.y + tt_c[s] * yh.y;
+            // one transform per star: the column of w1 (p contiguous), forward FFT along p
+#pragma unroll 1
+            for (int s0 = 0; s0 < G; s0 += UNITS) {
+                const int s = s0 + unit;
+                const bool act = s < G;
+                const int ss = act ? s : 0;
+                const C *src = fp.w1 + ((size_t)ss * Mh + k) * P;
+                C v[RR];
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int pp = t + LW * r - o;
+                    v[r] = act && pp >= 0 && pp < P ? __ldcg(src + pp) : C{0, 0};
                 }
-                __syncthreads();
+                const bool tt = fp.any_tt && act && s_star_tt[ss];
+                if (first_col && fp.any_tt) {
+                    R sb = 0, scs = 0;
+                    if (tt)
+                        for (int a0 = 0; a0 < P; a0 += LW * QC) {
+                            R pb[QC], pc[QC];
+#pragma unroll
+                            for (int u = 0; u < QC; ++u) {
+                                const int a = a0 + t + LW * u;
+                                pb[u] = a < P ? __ldcg(fp.pm + ((size_t)ss * P + a) * 2) : R(0);
+                                pc[u] = a < P ? __ldcg(fp.pm + ((size_t)ss * P + a) * 2 + 1) : R(0);
+                            }
+#pragma unroll
+                            for (int u = 0; u < QC; ++u) {
+                                sb += pb[u];
+                                scs += pc[u];
+                            }
+                        }
+#pragma unroll
+                    for (int off = LW / 2; off > 0; off >>= 1) {
+                        sb += __shfl_xor_sync(0xffffffffu, sb, off);
+                        scs += __shfl_xor_sync(0xffffffffu, scs, off);
+                    }
+                    if (tt && t == 0) {  // tip/tilt of the star, for this CTA's later columns
+                        s_ttb[ss] = sb;
+                        s_ttc[ss] = scs;
+                    }
+                }
+                __syncwarp();
+                wfft_fwd<M>(v, tw, t);
+                if (tt) {  // d_g -= b_g X(j, k) + c_g Y(j, k)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const int pos = r * LW + t;
+                        C xh, yh;
+                        if (first_col && xy_pre) {
+                            xh = xys[pos];
+                            yh = xys[M + pos];
+                        } else {
+                            xh = fp.xy_hat[((size_t)k << LOGM) + pos];
+                            yh = fp.xy_hat[((size_t)(Mh + k) << LOGM) + pos];
+                        }
+                        v[r].x -= s_ttb[ss] * xh.x + s_ttc[ss] * yh.x;
+                        v[r].y -= s_ttb[ss] * xh.y + s_ttc[ss] * yh.y;
+                    }
+                }
+                if (act)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) Dp[(size_t)s * M + r * LW + t] = v[r];
             }
-            if (stamp && tid == 0 && k == b) stamp[5] = gtimer();
+            SAFR_MARK(8, k == b);
+            __syncthreads();
+            SAFR_MARK(9, k == b);
             const C *Bcol;
             if (fp.stage_b) {
                 if (tid == 0) bar_flag = mbar_wait_bounded(&mbar, tma_phase, fp.timeout_ns, fp.status) ? 1 : -1;
@@ -384,90 +494,115 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
             } else {
                 Bcol = fp.B + (size_t)k * colB;
             }
-            // b_l(j) = sum_g B_lg(j) d_g(j) for each (group, layer), then inverse transforms along j
-            for (int base = 0; base < fp.ntask2; base += cap2) {
-                const int nact = min(cap2, fp.ntask2 - base);
-                for (int idx = tid; idx < (nact << LOGM); idx += NTH) {
-                    const int i = idx >> LOGM, j = idx & (M - 1);
-                    const int task = base + i, gi = task / L, l = task - gi * L;
-                    const GroupDev &gr = fp.grp[gi];
-                    const C *Bj = Bcol + ((size_t)(gr.b_row0 + l * gr.G) << LOGM) + j;
-                    R ar = 0, ai = 0;
-                    for (int gg = 0; gg < gr.G; ++gg) {
-                        const C bv = Bj[(size_t)gg << LOGM];
-                        const C dv = D[(size_t)gr.star[gg] * TS + j];
-                        ar += bv.x * dv.x - bv.y * dv.y;
-                        ai += bv.x * dv.y + bv.y * dv.x;
+            SAFR_MARK(10, k == b);
+            // one transform slot per (group, pair of layers): b_l = sum_g B_lg d_g (permuted j) for
+            // both layers from one read of d_g, then the inverse FFTs along j
+            const int half = (L + 1) >> 1, npair = fp.ngroups * half;
+            for (int u0 = 0; u0 < npair; u0 += UNITS) {
+                const int pt = u0 + unit;
+                const bool act = pt < npair;
+                const int ptk = act ? pt : 0, gi = ptk >= half ? 1 : 0, l0 = 2 * (ptk - gi * half);
+                const bool two_l = l0 + 1 < L;
+                const int gG = s_grp[gi].G;
+                const C *Bl = Bcol + ((size_t)(s_grp[gi].b_row0 + l0 * gG) << LOGM);
+                C v[RR], w[RR];
+#pragma unroll
+                for (int r = 0; r < RR; ++r) v[r] = w[r] = C{0, 0};
+                for (int gg = 0; gg < gG; ++gg) {
+                    const C *Bg = Bl + ((size_t)gg << LOGM);
+                    const C *Bh = Bg + ((size_t)(two_l ? gG : 0) << LOGM);
+                    const C *Dg = Dp + (size_t)s_grp[gi].star[gg] * M;
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const int pos = r * LW + t;
+                        const C dv = Dg[pos], bv = Bg[pos], bw = Bh[pos];
+                        v[r].x += bv.x * dv.x - bv.y * dv.y;
+                        v[r].y += bv.x * dv.y + bv.y * dv.x;
+                        w[r].x += bw.x * dv.x - bw.y * dv.y;
+                        w[r].y += bw.x * dv.y + bw.y * dv.x;
                     }
-                    Y[(size_t)i * TS + j] = C{ar, ai};
                 }
-                __syncthreads();
-                if (fp.energy)  // Parseval partial sums, one warp per (group, layer)
-                    for (int i = warp; i < nact; i += NTH / 32) {
-                        const int task = base + i, gi = task / L, l = task - gi * L;
-                        R e = 0;
-                        for (int j = lane; j < M; j += 32) {
-                            const C v = Y[(size_t)i * TS + j];
-                            e += v.x * v.x + v.y * v.y;
-                        }
-                        for (int off = 16; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
-                        if (lane == 0) fp.energy[((size_t)gi * L + l) * Mh + k] = (float)(k == 0 ? e : R(2) * e);
+                SAFR_MARK(11, k == b && u0 == 0);
+                if (fp.energy) {  // Parseval partial sums of |b_l(j, k)|^2 over j
+                    R e0 = 0, e1 = 0;
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        e0 += v[r].x * v[r].x + v[r].y * v[r].y;
+                        e1 += w[r].x * w[r].x + w[r].y * w[r].y;
                     }
-                fft_core<M>(Y, nact, 1, twq);
-                for (int idx = tid; idx < (nact << LOGM); idx += NTH) {
-                    const int i = idx >> LOGM, p = idx & (M - 1);
-                    const int task = base + i, gi = task / L, l = task - gi * L;
-                    fp.w2[((((size_t)gi * L + l) * Mh + k) << LOGM) + p] = Y[(size_t)i * TS + p];
+#pragma unroll
+                    for (int off = LW / 2; off > 0; off >>= 1) {
+                        e0 += __shfl_xor_sync(0xffffffffu, e0, off);
+                        e1 += __shfl_xor_sync(0xffffffffu, e1, off);
+                    }
+                    if (act && t == 0) {
+                        float *en = fp.energy + ((size_t)gi * L + l0) * Mh + k;
+                        en[0] = (float)(k == 0 ? e0 : R(2) * e0);
+                        if (two_l) en[Mh] = (float)(k == 0 ? e1 : R(2) * e1);
+                    }
                 }
+                // both layers through one copy of the transform code
+#pragma unroll 1
+                for (int q = 0; q < 2; ++q) {
+                    C x[RR];
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) x[r] = q ? w[r] : v[r];
+                    wfft_inv<M>(x, tw, t);
+                    if (act && (q == 0 || two_l)) {
+                        C *dst = fp.w2 + ((((size_t)gi * L + l0 + q) * Mh + k) << LOGM);
+#pragma unroll
+                        for (int r = 0; r < RR; ++r) dst[t + LW * r] = x[r];
+                    }
+                }
+                SAFR_MARK(12, k == b && u0 == 0);
+            }
+            SAFR_MARK(13, k == b);
+            // next column of this CTA: B block and column spectra are free once every warp is done
+            if (k + nb < Mh) {
                 __syncthreads();
-            }
-            // next column of this CTA: bring its B block in while the rest runs
-            if (fp.stage_b && k + nb < Mh) {
-                if (tid == 0) {
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    const C *src = fp.B + (size_t)(k + nb) * colB;
-                    mbar_expect_tx(&mbar, colB_bytes);
-                    for (unsigned off = 0; off < colB_bytes; off += 32768u)
-                        tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off,
-                                    min(32768u, colB_bytes - off), &mbar);
+                if (fp.stage_b) {
+                    if (tid == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        copy_b(k + nb);
+                    }
+                    tma_pending = true;
                 }
-                tma_pending = true;
             }
+            first_col = false;
         }
     }
-    if (stamp) {
-        __syncthreads();
-        if (tid == 0) stamp[6] = gtimer();
-    }
-    if (!grid_sync_bounded(fp.bar, epoch_s, 1, fp.status, fp.timeout_ns, &bar_flag)) {
+    SAFR_MARK(14, true);
+    if (!grid_sync_bounded(fp.bar, epoch, 1, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 15 : nullptr)) {
         drain();
         return;
     }
-    if (stamp && tid == 0) stamp[7] = gtimer();
+    SAFR_MARK(16, true);
     if (b == 0 && tid == 0) {  // every CTA has read this launch's epoch: open the next one
-        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(fp.bar + 1), "l"(epoch_s + 1ull) : "memory");
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(fp.bar + 1), "l"(epoch + 1ull) : "memory");
     }
 
     // ---- phase 3: (layer, row tile) ----------------------------------------------
     {
         const int RT = fp.rt3;
-        int *ti0 = (int *)s3;                                   // [M]
-        R *tfw = (R *)(ti0 + M);                                // [M]
         const int st0 = fp.st3[0], st1 = fp.st3[1];
-        C *stg0 = (C *)(tfw + M);                               // [Mh][st0]
+        // staged rows: column k's run of source rows starts at k * st + skew(k); the skew
+        // spreads the permuted-order reads of the row transforms over the banks
+        C *stg0 = (C *)s3;                                      // [Mh][st0]
         C *stg1 = stg0 + (size_t)Mh * st0;                      // [Mh][st1]
-        C *Z = stg1 + (size_t)Mh * st1;                         // [cap3][TS] row-pair transforms
-        const bool rs0 = fp.grp[0].resample != 0;               // only an LGS group (group 0) is resampled
+        C *Z = stg1 + (size_t)Mh * st1;                         // [cap3][M] inverse row transforms
         const bool two = fp.ngroups > 1;
         for (int it = b; it < fp.n3; it += nb) {
             const int l = it / fp.tiles3, p0 = (it - l * fp.tiles3) * RT;
             const int nr = min(RT, M - p0);
-            if (rs0)
+            if (rs0 && !(it == b && rs_pre)) {  // tables of a later item (the first one came with the prologue)
+                __syncthreads();
                 for (int i = tid; i < M; i += NTH) {
                     ti0[i] = fp.rs_i0[l * M + i];
                     tfw[i] = fp.rs_w[l * M + i];
                 }
+            }
             __syncthreads();
+            SAFR_MARK(17, it == b);
             const int first0 = rs0 ? ti0[p0] : p0;
             const int nsrc0 = rs0 ? ti0[p0 + nr - 1] + 2 - first0 : nr;
             const int nsrc1 = two ? nr : 0;  // the NGS group is never resampled
@@ -477,60 +612,91 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 if (tid == 0) atomicExch(fp.status, (int)SAFR_ERR_DEVICE);
                 continue;
             }
-            // stage the needed rows of every column: stg[k][s] = w2[gi][l][k][first + s]
+            // stage the needed rows of every column, one warp per column k:
+            // stg0[k][s] = w2[0][l][k][first0 + s], stg1[k][s] = w2[1][l][k][p0 + s]
             {
                 const C *src0 = fp.w2 + (size_t)l * Mh * M;
-                for (int idx = tid; idx < Mh * nsrc0; idx += NTH) {
-                    const int k = idx / nsrc0, s = idx - k * nsrc0;
-                    stg0[k * st0 + s] = __ldcg(src0 + ((size_t)k << LOGM) + ((first0 + s) & (M - 1)));
-                }
                 const C *src1 = fp.w2 + ((size_t)L + l) * Mh * M;
-                for (int idx = tid; idx < Mh * nsrc1; idx += NTH) {
-                    const int k = idx / nsrc1, s = idx - k * nsrc1;
-                    stg1[k * st1 + s] = __ldcg(src1 + ((size_t)k << LOGM) + p0 + s);
-                }
+                constexpr int KW = (Mh + NW - 1) / NW;  // columns per warp
+                constexpr int KB = KW < 8 ? KW : 8;     // of which in flight at once
+                for (int s = lane; s < nsrc0 || s < nsrc1; s += 32)
+                    for (int t0 = 0; t0 < KW; t0 += KB) {
+                        C v0[KB], v1[KB];
+#pragma unroll
+                        for (int u = 0; u < KB; ++u) {
+                            const int k = warp + NW * (t0 + u);
+                            if (k < Mh && s < nsrc0) v0[u] = __ldcg(src0 + ((size_t)k << LOGM) + ((first0 + s) & (M - 1)));
+                            if (k < Mh && s < nsrc1) v1[u] = __ldcg(src1 + ((size_t)k << LOGM) + p0 + s);
+                        }
+#pragma unroll
+                        for (int u = 0; u < KB; ++u) {
+                            const int k = warp + NW * (t0 + u);
+                            const int sk = ((k / RR) >> 1) & 15;
+                            if (k < Mh && s < nsrc0) stg0[k * st0 + sk + s] = v0[u];
+                            if (k < Mh && s < nsrc1) stg1[k * st1 + sk + s] = v1[u];
+                        }
+                    }
             }
             __syncthreads();
-            if (stamp && tid == 0 && it == b) stamp[8] = gtimer();
-            // Z[k] = X1[k] + i X2[k] over the full length M from the stored half spectra of a row pair
-            for (int idx = tid; idx < (ntot << LOGM); idx += NTH) {
-                const int task = idx >> LOGM, k = idx & (M - 1);
+            SAFR_MARK(18, it == b);
+            // one inverse transform per source row pair: Z[k] = X1[k] + i X2[k] over the
+            // full length M from the stored half spectra, built directly in the permuted order
+            for (int u0 = 0; u0 < ntot; u0 += UNITS) {
+                const int task = u0 + unit;
+                const bool act = task < ntot;
                 const bool g1 = task >= npair0;
                 const int i = g1 ? task - npair0 : task;
                 const C *sg = g1 ? stg1 : stg0;
                 const int st = g1 ? st1 : st0;
                 const bool hasb = 2 * i + 1 < (g1 ? nsrc1 : nsrc0);
-                C z = C{0, 0};
-                if (k < Mh) {
-                    C x1 = sg[k * st + 2 * i];
-                    C x2 = hasb ? sg[k * st + 2 * i + 1] : C{0, 0};
-                    if (k == 0) {
-                        x1.y = 0;
-                        x2.y = 0;
+                C v[RR];
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int k = r + RR * bt;
+                    C z = C{0, 0};
+                    if (act && k < Mh) {
+                        const C *row = sg + k * st + (((k / RR) >> 1) & 15);
+                        C x1 = row[2 * i];
+                        C x2 = hasb ? row[2 * i + 1] : C{0, 0};
+                        if (k == 0) {
+                            x1.y = 0;
+                            x2.y = 0;
+                        }
+                        z = C{x1.x - x2.y, x1.y + x2.x};
+                    } else if (act && k > Mh) {
+                        const int kk = M - k;
+                        const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
+                        const C x1 = row[2 * i];
+                        const C x2 = hasb ? row[2 * i + 1] : C{0, 0};
+                        z = C{x1.x + x2.y, x2.x - x1.y};
                     }
-                    z = C{x1.x - x2.y, x1.y + x2.x};
-                } else if (k > Mh) {
-                    const int kk = M - k;
-                    const C x1 = sg[kk * st + 2 * i];
-                    const C x2 = hasb ? sg[kk * st + 2 * i + 1] : C{0, 0};
-                    z = C{x1.x + x2.y, x2.x - x1.y};
+                    v[r] = z;
                 }
-                Z[(size_t)task * TS + k] = z;
+                wfft_inv<M>(v, tw, t);
+                if (act)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) Z[(size_t)task * M + t + LW * r] = v[r];
             }
+            SAFR_MARK(19, it == b);
             __syncthreads();
-            fft_core<M>(Z, ntot, 1, twq);
-            if (stamp && tid == 0 && it == b) stamp[9] = gtimer();
+            SAFR_MARK(20, it == b);
             R inv_scale = R(1);
-            if (fp.out_scales) {
-                // layer energy sum_n |b(n)|^2 over the groups (fixed order) -> mean square / M^4
+            if constexpr (std::is_same<TOUT, __half>::value) {
+                // layer energy sum_n |b(n)|^2 over the groups (fixed order) -> RMS = sqrt(energy) / M^2;
+                // scale = 2^round(log2 RMS): 2^(e-1) for RMS = f 2^e, f in [1/2, 1), rounded at f = 2^-1/2
                 R e = 0;
                 for (int gi = 0; gi < fp.ngroups; ++gi)
                     for (int k = tid; k < Mh; k += NTH) e += (R)__ldcg(fp.energy + ((size_t)gi * L + l) * Mh + k);
                 e = block_sum(e, red);
-                const double ms = (double)e / ((double)M * M * (double)M * M);
-                const double sc = ms > 0 ? exp2(rint(0.5 * log2(ms))) : 1.0;
-                inv_scale = (R)(1.0 / sc);
-                if (p0 == 0 && tid == 0) fp.out_scales[l] = (float)sc;
+                const float rms = sqrtf((float)e) / ((float)M * (float)M);
+                float sc = 1.0f;
+                if (rms > 0.0f && rms < INFINITY) {
+                    int ex;
+                    const float f = frexpf(rms, &ex);
+                    sc = ldexpf(1.0f, f < 0.70710678f ? ex - 1 : ex);
+                }
+                inv_scale = (R)(1.0f / sc);
+                if (p0 == 0 && tid == 0) fp.out_scales[l] = sc;
             }
             // source row s of group 0 is Z[s / 2] (real part for even s, imaginary for odd)
             const R f = fp.inv_M2 * inv_scale;
@@ -543,16 +709,16 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                     const int j0u = ti0[q];
                     const int ja = j0u & (M - 1), jb = (j0u + 1) & (M - 1);
                     const int s0 = ti0[p0 + r] - first0, s1 = s0 + 1;
-                    const C *za = Z + (size_t)(s0 >> 1) * TS, *zb = Z + (size_t)(s1 >> 1) * TS;
+                    const C *za = Z + (size_t)(s0 >> 1) * M, *zb = Z + (size_t)(s1 >> 1) * M;
                     const R a0 = (s0 & 1) ? za[ja].y : za[ja].x, a1 = (s0 & 1) ? za[jb].y : za[jb].x;
                     const R b0v = (s1 & 1) ? zb[ja].y : zb[ja].x, b1v = (s1 & 1) ? zb[jb].y : zb[jb].x;
                     v = (R(1) - fu) * ((R(1) - fv) * a0 + fv * a1) + fu * ((R(1) - fv) * b0v + fv * b1v);
                 } else {
-                    const C zz = Z[(size_t)(r >> 1) * TS + q];
+                    const C zz = Z[(size_t)(r >> 1) * M + q];
                     v = (r & 1) ? zz.y : zz.x;
                 }
                 if (two) {  // the NGS group's rows follow group 0's pairs
-                    const C zz = Z[(size_t)(npair0 + (r >> 1)) * TS + q];
+                    const C zz = Z[(size_t)(npair0 + (r >> 1)) * M + q];
                     v += (r & 1) ? zz.y : zz.x;
                 }
                 if constexpr (std::is_same<TOUT, double>::value)
@@ -561,9 +727,11 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                     store_out<TOUT>(outp + idx, (float)(v * f));
             }
             __syncthreads();
+            SAFR_MARK(21, it == b);
         }
     }
-    if (stamp && tid == 0) stamp[10] = gtimer();
+    SAFR_MARK(22, true);
+#undef SAFR_MARK
 }
 
 // ----------------------------------------------------------------------------
@@ -572,7 +740,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
 template <int M, typename R>
 struct Frame2Host {
     using C = typename Frame2Params<R>::C;
-    using S = FftShape<M>;
+    using S = WShape<M>;
 
     // phase-3 staged-row stride: at least n, odd (conflict-free column reads)
     static int odd_at_least(int n) { return n | 1; }
@@ -580,25 +748,35 @@ struct Frame2Host {
     // Sizes the kernel for the plan; false if it cannot hold it.
     static bool configure(safr_plan_s *pl, int nsm, void *kernel)
     {
-        const int Mh = M / 2, G = pl->G, L = pl->L, P = pl->P;
+        const int Mh = M / 2, G = pl->G, L = pl->L;
         const size_t cs = sizeof(C), rs = sizeof(R);
         const size_t limit = 227 * 1024 - 1024;  // dynamic shared memory budget
-        const int SLOTS = 512 / S::R1;
+        const int units = 16 * S::TPW;             // transforms in flight per CTA
         const int nb = nsm;
         auto al = [](size_t x) { return (x + 127) & ~(size_t)127; };
-        const size_t twq_b = al((size_t)M * cs);
-        // phase 1 / 2 scratch, sized for the transforms actually in flight
-        const int n1 = G * ((P + 1) / 2);
-        const int cap1 = std::min(SLOTS, (n1 + nb - 1) / nb);
-        const int cap2 = std::min(SLOTS, pl->ngroups * L);
-        const size_t s1 = (size_t)cap1 * S::TS * cs;
-        const size_t s2 = (size_t)G * S::TS * cs + (size_t)cap2 * S::TS * cs;
-        const size_t s12 = al(std::max(s1, s2));
+        if (G > SAFR_MAX_G) return false;
+        // phase 1 / 2: B column block, column spectra, removeTT stash
+        bool any_rs = false;
+        for (int gi = 0; gi < pl->ngroups; ++gi) any_rs |= pl->grp[gi].resample;
+        const size_t rsb = any_rs ? al((size_t)M * (4 + rs)) : 0;  // resample tables (whole kernel)
         const size_t colB = (size_t)pl->sumLG * M * cs;
-        if (G > 32) return false;
-        // phase 3 tiles
+        const size_t db = al((size_t)G * M * cs);
+        const size_t xyb = pl->remove_tt ? al(2 * (size_t)M * cs) : 0;
+        const bool stage = rsb + al(colB) + db + xyb <= limit;
+        pl->f2_stage_b = stage ? 1 : 0;
+        pl->f2_off_rs = 0;
+        pl->f2_off_b = (unsigned)rsb;
+        pl->f2_off_d = (unsigned)(rsb + (stage ? al(colB) : 0));
+        pl->f2_off_xy = pl->f2_off_d + (unsigned)db;
+        const size_t s12 = pl->f2_off_xy + xyb;
+        if (s12 > limit) return false;
+        // phase 3 tiles: every CTA takes ceil(items / grid) items one after the
+        // other, each with ceil(pairs / units) rounds of transforms; minimise
+        // rounds x (rows per item + about 4 rows of fixed cost + about 6 rows per
+        // transform round)
         int best_rt = 0;
         size_t best_s3 = 0;
+        long long best_cost = 0;
         int st[2] = {0, 0}, ns[2] = {0, 0};
         for (int rt = std::min(32, M); rt >= 2; rt -= 2) {
             int nsm_[2] = {0, 0};
@@ -616,36 +794,27 @@ struct Frame2Host {
                     }
                 nsm_[gi] = mx + (mx & 1);  // even: whole row pairs
             }
-            size_t s3 = (size_t)M * (4 + rs);
-            for (int gi = 0; gi < pl->ngroups; ++gi) s3 += (size_t)Mh * odd_at_least(nsm_[gi]) * cs;
-            const int cap3 = (nsm_[0] + nsm_[1]) / 2;  // every row pair of a tile in one batch
-            if (cap3 > SLOTS) continue;
-            s3 += (size_t)cap3 * S::TS * cs;
+            const int cap3 = (nsm_[0] + nsm_[1]) / 2;  // row pairs of one item
+            size_t s3 = rsb;
+            for (int gi = 0; gi < pl->ngroups; ++gi) s3 += (size_t)Mh * odd_at_least(nsm_[gi] + 15) * cs;
+            s3 += (size_t)cap3 * M * cs;
             s3 = al(s3);
             const long long items = (long long)L * ((M + rt - 1) / rt);
-            // largest tile that fits and still gives every CTA an item
-            if (twq_b + s3 <= limit && (items >= nb || rt == 2 || best_rt == 0)) {
-                if (best_rt == 0 || items >= nb) {
-                    best_rt = rt;
-                    best_s3 = s3;
-                    pl->f2_cap3 = cap3;
-                    for (int gi = 0; gi < 2; ++gi) {
-                        ns[gi] = nsm_[gi];
-                        st[gi] = gi < pl->ngroups ? odd_at_least(nsm_[gi]) : 0;
-                    }
-                    if (items >= nb) break;
+            const long long cost = ((items + nb - 1) / nb) * (rt + 4 + 6LL * ((cap3 + units - 1) / units));
+            if (s3 <= limit && (best_rt == 0 || cost <= best_cost)) {
+                best_cost = cost;
+                best_rt = rt;
+                best_s3 = s3;
+                pl->f2_cap3 = cap3;
+                for (int gi = 0; gi < 2; ++gi) {
+                    ns[gi] = nsm_[gi];
+                    st[gi] = gi < pl->ngroups ? odd_at_least(nsm_[gi] + 15) : 0;  // room for the skew
                 }
             }
         }
         if (best_rt == 0) return false;
-        // B staging if it fits beside the phase 1/2 scratch
-        const bool stage = twq_b + al(colB) + s12 <= limit;
-        pl->f2_stage_b = stage ? 1 : 0;
-        pl->f2_off_b = (unsigned)twq_b;
-        pl->f2_off_s12 = (unsigned)(twq_b + (stage ? al(colB) : 0));
-        pl->f2_off_s3 = (unsigned)twq_b;
-        const size_t total = std::max((size_t)pl->f2_off_s12 + s12, twq_b + best_s3);
-        if (total > limit) return false;
+        pl->f2_off_s3 = (unsigned)rsb;
+        const size_t total = std::max(s12, best_s3);
         pl->f2_smem = total;
         pl->f2_rt3 = best_rt;
         pl->f2_tiles3 = (M + best_rt - 1) / best_rt;
@@ -655,7 +824,6 @@ struct Frame2Host {
             pl->f2_nsrc3[gi] = ns[gi];
         }
         pl->f2_grid = nb;
-        (void)P;
         if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total) != cudaSuccess) {
             cudaGetLastError();
             return false;
@@ -696,8 +864,10 @@ struct Frame2Host {
         fp.skip_cta = pl->debug_skip_cta;
         fp.timeout_ns = pl->barrier_timeout_ns;
         fp.inv_M2 = (R)(1.0 / ((double)M * M));
+        fp.off_rs = pl->f2_off_rs;
         fp.off_b = pl->f2_off_b;
-        fp.off_s12 = pl->f2_off_s12;
+        fp.off_d = pl->f2_off_d;
+        fp.off_xy = pl->f2_off_xy;
         fp.off_s3 = pl->f2_off_s3;
         fp.in = in;
         fp.in_scales = in_scales;
@@ -727,21 +897,24 @@ struct Frame2Host {
     }
 };
 
-// Host-side table of the four-step twiddles W_M^(n1 k2), laid out [k2][n1].
+// Host-side table of the warp-FFT twiddles (WTw layout): W_M^(t k_r) at
+// [k_r * LW + t] for k_r < M / LW, then W_LW^e at [M + e], from FP64.
 inline void frame2_twiddles_impl(int M, std::vector<double> &re, std::vector<double> &im)
 {
-    int logM = 0;
-    while ((1 << logM) < M) ++logM;
-    const int R1 = 1 << (logM / 2), R2 = M / R1;
-    re.assign(M, 0.0);
-    im.assign(M, 0.0);
+    const int LW = wfft_lanes(M), R = M / LW;
+    re.assign(M + LW, 0.0);
+    im.assign(M + LW, 0.0);
     const double pi = 3.14159265358979323846264338327950288;
-    for (int k2 = 0; k2 < R2; ++k2)
-        for (int n1 = 0; n1 < R1; ++n1) {
-            const long long e = ((long long)n1 * k2) % M;
-            re[k2 * R1 + n1] = std::cos(2.0 * pi * (double)e / M);
-            im[k2 * R1 + n1] = -std::sin(2.0 * pi * (double)e / M);
+    for (int k = 0; k < R; ++k)
+        for (int t = 0; t < LW; ++t) {
+            const long long e = ((long long)t * k) % M;
+            re[k * LW + t] = std::cos(2.0 * pi * (double)e / M);
+            im[k * LW + t] = -std::sin(2.0 * pi * (double)e / M);
         }
+    for (int e = 0; e < LW; ++e) {
+        re[M + e] = std::cos(2.0 * pi * (double)e / LW);
+        im[M + e] = -std::sin(2.0 * pi * (double)e / LW);
+    }
 }
 
 }  // namespace safr

@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "frame_impl.cuh"
+#include "freqorder.h"
 #include "plan.h"
 #include "safr.h"
 
@@ -41,16 +42,20 @@ void *g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, 
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Twiddles W_M^(n1 k2) of the four-step FFT, laid out [k2][n1] (R1 = 2^floor(log2(M)/2)),
-// from FP64 sincospi, and the grid-barrier counters cleared for this call.
-__global__ void k_noalloc_prepare(float2 *twq, int M, int R1, unsigned long long *bar)
+// Warp-FFT twiddles from FP64 sincospi: W_M^(t k) at [k * LW + t] for k < M / LW,
+// then W_LW^e at [M + e] (LW = min(M, 32)); and the grid-barrier counters
+// cleared for this call.
+__global__ void k_noalloc_prepare(float2 *twq, int M, int LW, unsigned long long *bar)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double s = 0.0, c = 1.0;
     if (i < M) {
-        const int k2 = i / R1, n1 = i - k2 * R1;
-        const long long e = ((long long)n1 * k2) % M;
-        double s, c;
+        const int k = i / LW, t = i - k * LW;
+        const long long e = ((long long)t * k) % M;
         sincospi(2.0 * (double)e / (double)M, &s, &c);
+        twq[i] = make_float2((float)c, (float)-s);
+    } else if (i < M + LW) {
+        sincospi(2.0 * (double)(i - M) / (double)LW, &s, &c);
         twq[i] = make_float2((float)c, (float)-s);
     }
     if (i == 0) {
@@ -76,7 +81,8 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
     const int Mh = M / 2;
     // scratch carve-up: barrier counters | twiddles | row spectra w1 | layer spectra w2
     const size_t off_twq = 256;
-    const size_t off_w1 = off_twq + align256((size_t)M * sizeof(float2));
+    const int LW = safr::wfft_lanes(M);
+    const size_t off_w1 = off_twq + align256((size_t)(M + LW) * sizeof(float2));
     const size_t off_w2 = off_w1 + align256((size_t)G * Mh * P * sizeof(float2));
     const size_t need = off_w2 + align256((size_t)L * Mh * M * sizeof(float2));
     if (need > (size_t)SAFR_NOALLOC_SCRATCH_BYTES) return SAFR_ERR_UNSUPPORTED_SIZE;
@@ -167,8 +173,10 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
     fp.skip_cta = -1;
     fp.timeout_ns = 1000000000ull;
     fp.inv_M2 = (float)(1.0 / ((double)M * M));
+    fp.off_rs = pl.f2_off_rs;
     fp.off_b = pl.f2_off_b;
-    fp.off_s12 = pl.f2_off_s12;
+    fp.off_d = pl.f2_off_d;
+    fp.off_xy = pl.f2_off_xy;
     fp.off_s3 = pl.f2_off_s3;
     fp.in = d_wavefronts;
     fp.out = d_layers;
@@ -183,11 +191,8 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
     fp.grp[0].resample = 0;
     for (int g = 0; g < G; ++g) fp.grp[0].star[g] = g;
 
-    int logM = 0;
-    while ((1 << logM) < M) ++logM;
-    const int R1 = 1 << (logM / 2);
-    k_noalloc_prepare<<<(M + 255) / 256, 256, 0, stream>>>((float2 *)(scratch + off_twq), M, R1,
-                                                             (unsigned long long *)scratch);
+    k_noalloc_prepare<<<(M + LW + 255) / 256, 256, 0, stream>>>((float2 *)(scratch + off_twq), M, LW,
+                                                                  (unsigned long long *)scratch);
     if (cudaGetLastError() != cudaSuccess) return SAFR_ERR_CUDA;
     void *args[] = {&fp};
     if (cudaLaunchCooperativeKernel(kernel, dim3(pl.f2_grid), dim3(512), args, pl.f2_smem, stream) != cudaSuccess) {

@@ -10,7 +10,7 @@
 #include "safr.h"
 
 // timestamps a traced persistent-kernel frame records per CTA
-#define SAFR_TRACE_MARKS 11
+#define SAFR_TRACE_MARKS 23
 
 namespace safr {
 
@@ -98,7 +98,7 @@ struct safr_plan_s {
     // persistent-kernel shapes (frame_impl.cuh)
     int f2_grid = 0, f2_stage_b = 0, f2_rt3 = 2, f2_tiles3 = 1, f2_n3 = 1, f2_cap3 = 1;
     int f2_st3[2] = {0, 0}, f2_nsrc3[2] = {0, 0};
-    unsigned f2_off_b = 0, f2_off_s12 = 0, f2_off_s3 = 0;
+    unsigned f2_off_rs = 0, f2_off_b = 0, f2_off_d = 0, f2_off_s3 = 0, f2_off_xy = 0;
     size_t f2_smem = 0;
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
@@ -107,7 +107,7 @@ struct safr_plan_s {
     int k1_rows = 8;
 
     // device memory owned by the plan
-    void *d_B = nullptr;
+    void *d_B = nullptr;  // [Mh][sumLG][M], j in the warp-FFT order of freqorder.h
     size_t b_bytes = 0;
     void *d_w1 = nullptr, *d_w2 = nullptr;
     float *d_energy = nullptr;
@@ -117,8 +117,8 @@ struct safr_plan_s {
     void *d_rs_w = nullptr;
     unsigned char *d_mask = nullptr;
     void *d_tt_w = nullptr;
-    void *d_twq = nullptr;     // [M] four-step twiddles of the persistent kernel
-    void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT)
+    void *d_twq = nullptr;     // [M + min(M, 32)] warp-FFT twiddles of the persistent kernel
+    void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT), j permuted
     void *d_pm = nullptr;      // [G][P][2] per-row tip/tilt functionals
     unsigned long long *d_bar = nullptr; // grid barrier: arrival count, launch epoch
     unsigned long long *d_stamps = nullptr;  // [grid][SAFR_TRACE_MARKS] timestamps of traced fused frames

@@ -10,10 +10,12 @@
 // thread forms the G x G Hermitian matrix K = A A^H + alpha I, factors it by
 // Cholesky (K = C C^H) and solves K x_l = a_l for every column a_l of A:
 // B_lg = s_l conj(x_l[g]).  Everything is FP64; B is stored in the frame
-// kernels' precision.  Layout: B[k][b_row0 + l*G + g][j], k in [0, M/2).
+// kernels' precision.  Layout: B[k][b_row0 + l*G + g][pos(j)], k in [0, M/2), with
+// j in the warp-FFT order of freqorder.h.
 // The Nyquist row j = M/2 is zero (and the Nyquist column k = M/2 is not stored).
 #include <cuda_runtime.h>
 
+#include "freqorder.h"
 #include "plan.h"
 
 namespace safr {
@@ -33,7 +35,8 @@ __global__ void __launch_bounds__(128) precompute_kernel(int M, int Mh, int sumL
     if (idx >= (long)M * Mh) return;
     const int j = (int)(idx % M), k = (int)(idx / M);
     const int G = gr.G, L = gr.L;
-    C *Bk = B + ((size_t)k * sumLG + gr.b_row0) * M + j;
+    // stored with j in the frame kernels' warp-FFT order
+    C *Bk = B + ((size_t)k * sumLG + gr.b_row0) * M + wfft_pos_of_j(j, M);
     if (j == M / 2) {
         for (int r = 0; r < L * G; ++r) store_c(Bk + (size_t)r * M, 0.0, 0.0);
         return;

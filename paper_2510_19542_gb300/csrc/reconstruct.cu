@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "freqorder.h"
 #include "plan.h"
 
 namespace safr {
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(256) k_cols_apply(FrameParams<R> fp)
 #pragma unroll
             for (int t = 0; t < GMAX; ++t)
                 if (t < Gg) d[t] = dcol[(t << logM) + j];
-            const C *Bj = Bk + (size_t)l0 * Gg * M + j;
+            // B is stored with j in the persistent kernel's warp-FFT order
+            const C *Bj = Bk + (size_t)l0 * Gg * M + wfft_pos_of_j(j, M);
 #pragma unroll 2
             for (int l = 0; l < lc; ++l) {
                 C bv[GMAX];

@@ -1,0 +1,211 @@
+// Warp-level FFTs of compile-time length M for the persistent frame kernel.
+//
+// A transform of length M = LW * R (LW = min(M, 32) lanes, R = M / LW values
+// per lane) runs in one group of LW lanes with all data in registers:
+//
+//   forward, natural order in, permuted order out.  Lane t holds x[t + LW r]
+//     in register r.  Step A: R-point DFT over r in registers, then multiply
+//     register k_r by W_M^(t k_r).  Step B: LW-point DFT across the lanes by
+//     radix-2 decimation in frequency with __shfl_xor_sync.  Lane t ends with
+//     X[k_r + R brev(t)] in register k_r (brev: reversal of log2(LW) bits).
+//   inverse, permuted order in, natural order out: the same steps in reverse
+//     with conjugate twiddles, unnormalised.  Lane t ends with
+//     y[t + LW r] = sum_k Y[k] W_M^(-k (t + LW r)) in register r.
+//
+// This is the four-step factorisation of the DFT with N1 = LW, N2 = R:
+//   X[k2 + R k1] = sum_t W_LW^(t k1) W_M^(t k2) sum_r W_R^(r k2) x[t + LW r].
+// No shared memory and no block barrier: every lane of the warp must call the
+// functions together (lanes of unused transforms compute on any values).
+// The R-point DFTs are recursive radix-2 decimation in time, fully unrolled,
+// with the exact constants cos(pi m / 16); the lane-stage twiddles W_LW^e are
+// the same constants; the W_M^(t k_r) twiddles come from a table built on the
+// host in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace safr {
+
+// cos(pi m / 16), m = 0..8
+__host__ __device__ constexpr double cos_pi16(int m)
+{
+    return m == 0 ? 1.0
+         : m == 1 ? 0.98078528040323044912618223613424
+         : m == 2 ? 0.92387953251128675612818318939679
+         : m == 3 ? 0.83146961230254523707878837761791
+         : m == 4 ? 0.70710678118654752440084436210485
+         : m == 5 ? 0.55557023301960222474283081394853
+         : m == 6 ? 0.38268343236508977172845998403040
+         : m == 7 ? 0.19509032201612826784828486847702
+         : 0.0;
+}
+
+template <typename C>
+__device__ __forceinline__ C c_add(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C>
+__device__ __forceinline__ C c_sub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C>
+__device__ __forceinline__ C c_mul(C a, C b) { return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename C>
+__device__ __forceinline__ C c_mulc(C a, C b) { return C{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y}; }  // a conj(b)
+
+// v * W_N^k with W_N = exp(-2 pi i / N) (forward) or its conjugate (inverse), N <= 32
+template <int N, int K, bool INV, typename C>
+__device__ __forceinline__ C twiddle_const(C v)
+{
+    using R = decltype(v.x);
+    constexpr int m = (32 / N) * K;  // angle 2 pi K / N = pi m / 16, 0 <= m < 16
+    if constexpr (m == 0) {
+        return v;
+    } else if constexpr (m == 8) {  // -i (forward) / +i (inverse)
+        return INV ? C{-v.y, v.x} : C{v.y, -v.x};
+    } else {
+        constexpr double cd = m <= 8 ? cos_pi16(m) : -cos_pi16(16 - m);
+        constexpr double sd = m <= 8 ? cos_pi16(8 - m) : cos_pi16(m - 8);
+        const R c = (R)cd, s = INV ? (R)sd : (R)(-sd);
+        return C{v.x * c - v.y * s, v.x * s + v.y * c};
+    }
+}
+
+template <int N, int K, bool INV, typename C>
+__device__ __forceinline__ void dft_combine(C *v, const C *e, const C *o)
+{
+    if constexpr (K < N / 2) {
+        const C t = twiddle_const<N, K, INV>(o[K]);
+        v[K] = c_add(e[K], t);
+        v[K + N / 2] = c_sub(e[K], t);
+        dft_combine<N, K + 1, INV>(v, e, o);
+    }
+}
+
+// In-register DFT of N points (N = 1, 2, 4, 8, 16, 32), natural order in and out.
+template <int N, bool INV, typename C>
+__device__ __forceinline__ void dft_reg(C *v)
+{
+    if constexpr (N == 2) {
+        const C a = v[0];
+        v[0] = c_add(a, v[1]);
+        v[1] = c_sub(a, v[1]);
+    } else if constexpr (N > 2) {
+        C e[N / 2], o[N / 2];
+#pragma unroll
+        for (int i = 0; i < N / 2; ++i) {
+            e[i] = v[2 * i];
+            o[i] = v[2 * i + 1];
+        }
+        dft_reg<N / 2, INV>(e);
+        dft_reg<N / 2, INV>(o);
+        dft_combine<N, 0, INV>(v, e, o);
+    }
+}
+
+constexpr int ilog2c(int n) { return n <= 1 ? 0 : 1 + ilog2c(n / 2); }
+
+template <int M>
+struct WShape {
+    static constexpr int LW = M < 32 ? M : 32;  // lanes per transform
+    static constexpr int R = M / LW;            // values per lane
+    static constexpr int LB = ilog2c(LW);       // lane bits
+    static constexpr int TPW = 32 / LW;         // transforms per warp
+    static constexpr int LOG = ilog2c(M);
+};
+
+// exp(-2 pi i e / 32) for 0 <= e < 32, from the exact constants cos(pi m / 16).
+// Branches on e: fill a table with it once, do not call it per lane in a loop.
+template <typename C>
+__device__ __forceinline__ C w32(int e)
+{
+    using R = decltype(C{}.x);
+    auto cpi16 = [](int m) -> R {  // cos(pi m / 16), 0 <= m < 32
+        const int a = m & 15;
+        const int f = a <= 8 ? a : 16 - a;  // fold to [0, 8]
+        R v;
+        switch (f) {
+        case 0: v = (R)cos_pi16(0); break;
+        case 1: v = (R)cos_pi16(1); break;
+        case 2: v = (R)cos_pi16(2); break;
+        case 3: v = (R)cos_pi16(3); break;
+        case 4: v = (R)cos_pi16(4); break;
+        case 5: v = (R)cos_pi16(5); break;
+        case 6: v = (R)cos_pi16(6); break;
+        case 7: v = (R)cos_pi16(7); break;
+        default: v = (R)0; break;
+        }
+        // cos(pi m / 16) < 0 for m in (8, 24)
+        return (m > 8 && m < 24) ? -v : v;
+    };
+    return C{cpi16(e), -cpi16((e + 24) & 31)};  // sin(x) = cos(x - pi/2)
+}
+
+// Per-lane twiddles W_M^(t k_r) (table layout, host FP64: tab[k_r * LW + t]) and
+// the lane-stage twiddles W_32^e, e < 32 (a table in shared memory, filled by
+// wtw_fill_w32 before the first transform).
+template <int M, typename C>
+struct WTw {
+    using S = WShape<M>;
+    C tw[S::R];
+    const C *w32s;
+    __device__ __forceinline__ void load(const C *tab, const C *w32_table, int t)
+    {
+#pragma unroll
+        for (int k = 0; k < S::R; ++k) tw[k] = tab[k * S::LW + t];
+        w32s = w32_table;
+    }
+};
+
+// threads 0..31 of the block write W_32^e to table[e]
+template <typename C>
+__device__ __forceinline__ void wtw_fill_w32(C *table)
+{
+    if (threadIdx.x < 32) table[threadIdx.x] = w32<C>((int)threadIdx.x);
+}
+
+template <typename C>
+__device__ __forceinline__ C shfl_xor_c(C v, int m)
+{
+    return C{__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
+}
+
+// Forward transform, natural order in, permuted order out (see above).
+template <int M, typename C>
+__device__ __forceinline__ void wfft_fwd(C (&v)[WShape<M>::R], const WTw<M, C> &w, int t)
+{
+    using S = WShape<M>;
+    dft_reg<S::R, false>(v);
+#pragma unroll
+    for (int k = 1; k < S::R; ++k) v[k] = c_mul(v[k], w.tw[k]);
+    // stage h: W_(2h)^(t mod h) = W_32^((t mod h) * 16 / h)
+#pragma unroll 1
+    for (int h = S::LW / 2; h > 0; h >>= 1) {
+        const bool low = (t & h) != 0;
+        const C ws = w.w32s[(t & (h - 1)) * (16 / h)];
+#pragma unroll
+        for (int k = 0; k < S::R; ++k) {
+            const C p = shfl_xor_c(v[k], h);
+            v[k] = low ? c_mul(c_sub(p, v[k]), ws) : c_add(v[k], p);
+        }
+    }
+}
+
+// Inverse transform (unnormalised), permuted order in, natural order out.
+template <int M, typename C>
+__device__ __forceinline__ void wfft_inv(C (&v)[WShape<M>::R], const WTw<M, C> &w, int t)
+{
+    using S = WShape<M>;
+#pragma unroll 1
+    for (int h = 1; h < S::LW; h <<= 1) {
+        const bool low = (t & h) != 0;
+        const C ws = w.w32s[(t & (h - 1)) * (16 / h)];
+#pragma unroll
+        for (int k = 0; k < S::R; ++k) {
+            if (low) v[k] = c_mulc(v[k], ws);
+            const C p = shfl_xor_c(v[k], h);
+            v[k] = low ? c_sub(p, v[k]) : c_add(v[k], p);
+        }
+    }
+#pragma unroll
+    for (int k = 1; k < S::R; ++k) v[k] = c_mulc(v[k], w.tw[k]);
+    dft_reg<S::R, true>(v);
+}
+
+}  // namespace safr

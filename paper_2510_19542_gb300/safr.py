@@ -221,11 +221,12 @@ def safr_trace_read(plan: int):
 
 def safr_trace_phases(plan: int):
     """Phase completion times (us) of the last traced persistent-kernel frame."""
-    us = (C.c_double * 16)()
+    us = (C.c_double * 32)()
     n = C.c_int(0)
-    _check(load().safr_trace_phases(plan, us, 16, C.byref(n)), "safr_trace_phases")
-    keys = ["start", "prologue", "p1_first_fft", "p1_done", "bar1_out", "p2_fwd", "p2_done", "bar2_out",
-            "p3_staged", "p3_fft", "p3_done"]
+    _check(load().safr_trace_phases(plan, us, 32, C.byref(n)), "safr_trace_phases")
+    keys = ["start", "prologue", "p1_data_in", "p1_B_issued", "p1_fft", "p1_done", "bar1_arrive", "bar1_out",
+            "p2_star_fft", "p2_synced", "p2_B_landed", "p2_apply", "p2_inv_fft", "p2_stored", "p2_done",
+            "bar2_arrive", "bar2_out", "p3_tables", "p3_staged", "p3_fft", "p3_synced", "p3_first_stored", "p3_done"]
     return dict(zip(keys, [us[i] for i in range(n.value)]))
 
 

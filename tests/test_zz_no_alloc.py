@@ -40,6 +40,23 @@ def test_noalloc_rejects_sizes_beyond_the_scratch_without_a_gpu():
         safr.SAFR_ERR_MISALIGNED
 
 
+def _kernel_order(B):
+    """B from safr_copy_B (natural j, last axis) in the frame kernel's frequency
+    order along j: pos(j) = (j mod R) * LW + brev(j div R), LW = min(M, 32),
+    R = M / LW, brev reversing log2(LW) bits."""
+    M = B.shape[-1]
+    LW = min(M, 32)
+    R, bits = M // LW, LW.bit_length() - 1
+    j = np.arange(M)
+    m = j // R
+    brev = np.zeros_like(m)
+    for i in range(bits):
+        brev |= ((m >> i) & 1) << (bits - 1 - i)
+    out = np.empty_like(B)
+    out[..., (j % R) * LW + brev] = B
+    return out
+
+
 def _geometries(synth):
     ngs = dict(synth.scaled(synth.config(3), M=256, P=256, L=9), precision="fp32")
     tiny = dict(synth.config(1), precision="fp32")
@@ -63,7 +80,8 @@ def test_noalloc_matches_plan_entry_point_on_calls_in_a_row():
         assert info["ngroups"] == 1
         M, P, L, G = info["M"], info["P"], info["L"], info["G"]
         # B of the single group, [k][l][g][j], rounded to FP32 like the plan's own copy
-        B = torch.from_numpy(np.ascontiguousarray(safr.safr_copy_B(plan.handle, 0).astype(np.complex64))).to(dev)
+        B = torch.from_numpy(np.ascontiguousarray(_kernel_order(safr.safr_copy_B(plan.handle, 0)).astype(np.complex64)))
+        B = B.to(dev)
         status = torch.zeros(1, dtype=torch.int32, device=dev)
         for seed in (21, 22):  # two calls in a row on the shared scratch
             x = torch.from_numpy(synth.random_frame(g, seed).astype(np.float32)).to(dev)
