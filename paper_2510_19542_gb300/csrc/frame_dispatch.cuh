@@ -15,7 +15,7 @@ struct Frame2Inst {
     {
         Frame2Params<R> fp = Frame2Host<M, R>::params(pl, in, isc, out, osc);
         void *args[] = {&fp};
-        return cudaLaunchCooperativeKernel(kernel(), dim3(pl->f2_grid), dim3(512), args, pl->f2_smem, st);
+        return cudaLaunchCooperativeKernel(kernel(), dim3(pl->f2_grid), dim3(frame2_threads(M)), args, pl->f2_smem, st);
     }
 };
 

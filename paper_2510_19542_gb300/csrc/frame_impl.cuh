@@ -74,7 +74,7 @@ struct Frame2Params {
     unsigned long long timeout_ns;
     R inv_M2;
     // shared-memory carve-up (bytes from the dynamic base)
-    unsigned off_rs, off_b, off_d, off_xy, off_s3;
+    unsigned off_rs, off_tw, off_b, off_d, off_xy, off_s3;
     const void *in;
     const float *in_scales;
     void *out;
@@ -124,13 +124,6 @@ __device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned
         "l"(src), "r"(bytes), "r"(smem_u32(mbar))
         : "memory");
 }
-
-// 16-byte asynchronous copy global -> shared (bypassing registers); complete after cp_async_wait_all
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity)
 {
@@ -199,15 +192,20 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsig
 }
 
 
+// Threads per CTA of the persistent kernel for grid size M (16 warps: measured
+// faster than 32 warps with half the registers each at M = 256).
+__host__ __device__ constexpr int frame2_threads(int) { return 512; }
+
 template <int M, typename R, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
+__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R> fp)
 {
     using C = typename Frame2Params<R>::C;
     using S = WShape<M>;
     constexpr int LW = S::LW, RR = S::R, LB = S::LB;
     constexpr int Mh = M / 2;
     constexpr int LOGM = S::LOG;
-    constexpr int NTH = 512;
+    constexpr int NTH = frame2_threads(M);
+    constexpr int LPS = NTH >= 1024 ? 1 : 2;  // layers per transform slot in the phase-2 apply
     constexpr int NW = NTH / 32;
     constexpr int UNITS = NW * S::TPW;  // transforms in flight per CTA
     constexpr int QC = 4;               // per-lane loads in flight in the pupil loops
@@ -280,31 +278,36 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
     __shared__ C s_w32[32];
     wtw_fill_w32(s_w32);
     WTw<M, C> tw;
-    tw.load(fp.twq, s_w32, t);
-    // this CTA's first phase-2 column of the removeTT spectra and its first phase-3
-    // item's resample tables: asynchronous copies into shared memory of their own
+    // tables, one bulk copy each into shared memory of their own, completing on
+    // mbar_t: the warp-FFT twiddles, this CTA's first phase-2 column of the
+    // removeTT spectra and its first phase-3 item's resample tables
+    __shared__ __align__(8) uint64_t mbar_t;
+    C *twq_s = (C *)(smem + fp.off_tw);     // [M]
     int *ti0 = (int *)(smem + fp.off_rs);  // [M]
     R *tfw = (R *)(ti0 + M);               // [M]
     const bool xy_pre = fp.any_tt && b < Mh;
-    if (xy_pre) {
-        constexpr int CH = M * (int)sizeof(C) / 16;  // 16-byte chunks per row
-        for (int c = tid; c < 2 * CH; c += NTH) {
-            const int row = c / CH, off = c - row * CH;
-            cp_async16((unsigned char *)(xys + row * M) + off * 16,
-                       (const unsigned char *)(fp.xy_hat + ((size_t)(row * Mh + b) << LOGM)) + off * 16);
-        }
-    }
     const bool rs_pre = rs0 && b < fp.n3;
-    if (rs_pre) {
-        const int l = b / fp.tiles3;
-        constexpr int CI = M * 4 / 16, CW = M * (int)sizeof(R) / 16;
-        for (int c = tid; c < CI + CW; c += NTH) {
-            if (c < CI)
-                cp_async16((unsigned char *)ti0 + c * 16, (const unsigned char *)(fp.rs_i0 + (size_t)l * M) + c * 16);
-            else
-                cp_async16((unsigned char *)tfw + (c - CI) * 16, (const unsigned char *)(fp.rs_w + (size_t)l * M) + (c - CI) * 16);
+    if (tid == 0) {
+        mbar_init(&mbar_t, 1);
+        const unsigned cb = (unsigned)(M * sizeof(C)), ib = (unsigned)(M * 4), wb = (unsigned)(M * sizeof(R));
+        mbar_expect_tx(&mbar_t, cb + (xy_pre ? 2 * cb : 0u) + (rs_pre ? ib + wb : 0u));
+        tma_load_1d(twq_s, fp.twq, cb, &mbar_t);
+        if (xy_pre) {
+            tma_load_1d(xys, fp.xy_hat + ((size_t)b << LOGM), cb, &mbar_t);
+            tma_load_1d(xys + M, fp.xy_hat + ((size_t)(Mh + b) << LOGM), cb, &mbar_t);
+        }
+        if (rs_pre) {
+            const int l = b / fp.tiles3;
+            tma_load_1d(ti0, fp.rs_i0 + (size_t)l * M, ib, &mbar_t);
+            tma_load_1d(tfw, fp.rs_w + (size_t)l * M, wb, &mbar_t);
         }
     }
+    // every thread waits for the tables before its first transform (no thread leaves
+    // on a timeout here: the status word records it and the barriers stay balanced)
+    auto tables = [&]() {
+        mbar_wait_bounded(&mbar_t, 0, fp.timeout_ns, fp.status);
+        tw.load(twq_s, s_w32, t);
+    };
     {   // later columns of this CTA (or every column when B is not staged): into L2
         const int k0 = fp.stage_b ? b + nb : b;
         for (int k = k0; k < Mh; k += nb) {
@@ -375,6 +378,7 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
             // the frame data has landed: B streams in behind it
             if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);
             SAFR_MARK(3, first);
+            if (first) tables();
             wfft_fwd<M>(v, tw, t);
             SAFR_MARK(4, first);
             // Z[k] sits in register k_r of lane t for k = k_r + R brev(t); Z[M - k] in
@@ -400,8 +404,8 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
         }
         if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);  // a CTA without phase-1 rows
         if (fp.stage_b && b < Mh) tma_pending = true;
+        if (first) tables();  // a warp without phase-1 rows
     }
-    cp_async_wait_all();  // this thread's prologue copies (visible to the CTA after the barrier)
     if (b == fp.skip_cta) {  // test hook: every other CTA's first barrier must time out
         drain();
         return;
@@ -495,60 +499,56 @@ __global__ void __launch_bounds__(512, 1) k_frame2(Frame2Params<R> fp)
                 Bcol = fp.B + (size_t)k * colB;
             }
             SAFR_MARK(10, k == b);
-            // one transform slot per (group, pair of layers): b_l = sum_g B_lg d_g (permuted j) for
-            // both layers from one read of d_g, then the inverse FFTs along j
-            const int half = (L + 1) >> 1, npair = fp.ngroups * half;
-            for (int u0 = 0; u0 < npair; u0 += UNITS) {
+            // one transform slot per (group, LPS layers): b_l = sum_g B_lg d_g (permuted j) for
+            // the slot's layers from one read of d_g, then the inverse FFTs along j
+            const int per = (L + LPS - 1) / LPS, nslot = fp.ngroups * per;
+            for (int u0 = 0; u0 < nslot; u0 += UNITS) {
                 const int pt = u0 + unit;
-                const bool act = pt < npair;
-                const int ptk = act ? pt : 0, gi = ptk >= half ? 1 : 0, l0 = 2 * (ptk - gi * half);
-                const bool two_l = l0 + 1 < L;
+                const bool act = pt < nslot;
+                const int ptk = act ? pt : 0, gi = ptk >= per ? 1 : 0, l0 = LPS * (ptk - gi * per);
+                const int nl = min(LPS, L - l0);
                 const int gG = s_grp[gi].G;
                 const C *Bl = Bcol + ((size_t)(s_grp[gi].b_row0 + l0 * gG) << LOGM);
-                C v[RR], w[RR];
+                C v[LPS][RR];
 #pragma unroll
-                for (int r = 0; r < RR; ++r) v[r] = w[r] = C{0, 0};
+                for (int q = 0; q < LPS; ++q)
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) v[q][r] = C{0, 0};
                 for (int gg = 0; gg < gG; ++gg) {
-                    const C *Bg = Bl + ((size_t)gg << LOGM);
-                    const C *Bh = Bg + ((size_t)(two_l ? gG : 0) << LOGM);
                     const C *Dg = Dp + (size_t)s_grp[gi].star[gg] * M;
 #pragma unroll
                     for (int r = 0; r < RR; ++r) {
                         const int pos = r * LW + t;
-                        const C dv = Dg[pos], bv = Bg[pos], bw = Bh[pos];
-                        v[r].x += bv.x * dv.x - bv.y * dv.y;
-                        v[r].y += bv.x * dv.y + bv.y * dv.x;
-                        w[r].x += bw.x * dv.x - bw.y * dv.y;
-                        w[r].y += bw.x * dv.y + bw.y * dv.x;
+                        const C dv = Dg[pos];
+#pragma unroll
+                        for (int q = 0; q < LPS; ++q) {
+                            const C bv = Bl[((size_t)(gg + (q < nl ? q : 0) * gG) << LOGM) + pos];
+                            v[q][r].x += bv.x * dv.x - bv.y * dv.y;
+                            v[q][r].y += bv.x * dv.y + bv.y * dv.x;
+                        }
                     }
                 }
                 SAFR_MARK(11, k == b && u0 == 0);
                 if (fp.energy) {  // Parseval partial sums of |b_l(j, k)|^2 over j
-                    R e0 = 0, e1 = 0;
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        e0 += v[r].x * v[r].x + v[r].y * v[r].y;
-                        e1 += w[r].x * w[r].x + w[r].y * w[r].y;
-                    }
+                    for (int q = 0; q < LPS; ++q) {
+                        R e = 0;
 #pragma unroll
-                    for (int off = LW / 2; off > 0; off >>= 1) {
-                        e0 += __shfl_xor_sync(0xffffffffu, e0, off);
-                        e1 += __shfl_xor_sync(0xffffffffu, e1, off);
-                    }
-                    if (act && t == 0) {
-                        float *en = fp.energy + ((size_t)gi * L + l0) * Mh + k;
-                        en[0] = (float)(k == 0 ? e0 : R(2) * e0);
-                        if (two_l) en[Mh] = (float)(k == 0 ? e1 : R(2) * e1);
+                        for (int r = 0; r < RR; ++r) e += v[q][r].x * v[q][r].x + v[q][r].y * v[q][r].y;
+#pragma unroll
+                        for (int off = LW / 2; off > 0; off >>= 1) e += __shfl_xor_sync(0xffffffffu, e, off);
+                        if (act && t == 0 && q < nl)
+                            fp.energy[((size_t)gi * L + l0 + q) * Mh + k] = (float)(k == 0 ? e : R(2) * e);
                     }
                 }
-                // both layers through one copy of the transform code
+                // the slot's layers through one copy of the transform code
 #pragma unroll 1
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < LPS; ++q) {
                     C x[RR];
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) x[r] = q ? w[r] : v[r];
+                    for (int r = 0; r < RR; ++r) x[r] = (LPS == 1 || q == 0) ? v[0][r] : v[LPS - 1][r];
                     wfft_inv<M>(x, tw, t);
-                    if (act && (q == 0 || two_l)) {
+                    if (act && q < nl) {
                         C *dst = fp.w2 + ((((size_t)gi * L + l0 + q) * Mh + k) << LOGM);
 #pragma unroll
                         for (int r = 0; r < RR; ++r) dst[t + LW * r] = x[r];
@@ -751,20 +751,22 @@ struct Frame2Host {
         const int Mh = M / 2, G = pl->G, L = pl->L;
         const size_t cs = sizeof(C), rs = sizeof(R);
         const size_t limit = 227 * 1024 - 1024;  // dynamic shared memory budget
-        const int units = 16 * S::TPW;             // transforms in flight per CTA
+        const int units = frame2_threads(M) / 32 * S::TPW;  // transforms in flight per CTA
         const int nb = nsm;
         auto al = [](size_t x) { return (x + 127) & ~(size_t)127; };
         if (G > SAFR_MAX_G) return false;
         // phase 1 / 2: B column block, column spectra, removeTT stash
         bool any_rs = false;
         for (int gi = 0; gi < pl->ngroups; ++gi) any_rs |= pl->grp[gi].resample;
-        const size_t rsb = any_rs ? al((size_t)M * (4 + rs)) : 0;  // resample tables (whole kernel)
+        // resample tables (whole kernel), then the twiddle table (until the first transform)
+        const size_t rsb = (any_rs ? al((size_t)M * (4 + rs)) : 0) + al((size_t)M * cs);
         const size_t colB = (size_t)pl->sumLG * M * cs;
         const size_t db = al((size_t)G * M * cs);
         const size_t xyb = pl->remove_tt ? al(2 * (size_t)M * cs) : 0;
         const bool stage = rsb + al(colB) + db + xyb <= limit;
         pl->f2_stage_b = stage ? 1 : 0;
         pl->f2_off_rs = 0;
+        pl->f2_off_tw = (unsigned)(any_rs ? al((size_t)M * (4 + rs)) : 0);
         pl->f2_off_b = (unsigned)rsb;
         pl->f2_off_d = (unsigned)(rsb + (stage ? al(colB) : 0));
         pl->f2_off_xy = pl->f2_off_d + (unsigned)db;
@@ -829,7 +831,8 @@ struct Frame2Host {
             return false;
         }
         int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 512, total) != cudaSuccess || occ < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, frame2_threads(M), total) != cudaSuccess ||
+            occ < 1) {
             cudaGetLastError();
             return false;
         }
@@ -865,6 +868,7 @@ struct Frame2Host {
         fp.timeout_ns = pl->barrier_timeout_ns;
         fp.inv_M2 = (R)(1.0 / ((double)M * M));
         fp.off_rs = pl->f2_off_rs;
+        fp.off_tw = pl->f2_off_tw;
         fp.off_b = pl->f2_off_b;
         fp.off_d = pl->f2_off_d;
         fp.off_xy = pl->f2_off_xy;

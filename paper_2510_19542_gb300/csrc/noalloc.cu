@@ -174,6 +174,7 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
     fp.timeout_ns = 1000000000ull;
     fp.inv_M2 = (float)(1.0 / ((double)M * M));
     fp.off_rs = pl.f2_off_rs;
+    fp.off_tw = pl.f2_off_tw;
     fp.off_b = pl.f2_off_b;
     fp.off_d = pl.f2_off_d;
     fp.off_xy = pl.f2_off_xy;
@@ -195,7 +196,8 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
                                                                   (unsigned long long *)scratch);
     if (cudaGetLastError() != cudaSuccess) return SAFR_ERR_CUDA;
     void *args[] = {&fp};
-    if (cudaLaunchCooperativeKernel(kernel, dim3(pl.f2_grid), dim3(512), args, pl.f2_smem, stream) != cudaSuccess) {
+    if (cudaLaunchCooperativeKernel(kernel, dim3(pl.f2_grid), dim3(safr::frame2_threads(M)), args, pl.f2_smem,
+                                    stream) != cudaSuccess) {
         cudaGetLastError();
         return SAFR_ERR_CUDA;
     }

@@ -98,7 +98,7 @@ struct safr_plan_s {
     // persistent-kernel shapes (frame_impl.cuh)
     int f2_grid = 0, f2_stage_b = 0, f2_rt3 = 2, f2_tiles3 = 1, f2_n3 = 1, f2_cap3 = 1;
     int f2_st3[2] = {0, 0}, f2_nsrc3[2] = {0, 0};
-    unsigned f2_off_rs = 0, f2_off_b = 0, f2_off_d = 0, f2_off_s3 = 0, f2_off_xy = 0;
+    unsigned f2_off_rs = 0, f2_off_tw = 0, f2_off_b = 0, f2_off_d = 0, f2_off_s3 = 0, f2_off_xy = 0;
     size_t f2_smem = 0;
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
