@@ -177,12 +177,17 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[WShape<M>::R], const WTw<M, C> &
     // stage h: W_(2h)^(t mod h) = W_32^((t mod h) * 16 / h)
 #pragma unroll 1
     for (int h = S::LW / 2; h > 0; h >>= 1) {
+        // upper lane: v + p; lower lane: (p - v) W.  As (sg v + p) wp with sg = -1, wp = W on the
+        // lower lane and sg = 1, wp = 1 on the upper one.
+        using R = decltype(C{}.x);
         const bool low = (t & h) != 0;
         const C ws = w.w32s[(t & (h - 1)) * (16 / h)];
+        const C wp = low ? ws : C{R(1), R(0)};
+        const R sg = low ? R(-1) : R(1);
 #pragma unroll
         for (int k = 0; k < S::R; ++k) {
             const C p = shfl_xor_c(v[k], h);
-            v[k] = low ? c_mul(c_sub(p, v[k]), ws) : c_add(v[k], p);
+            v[k] = c_mul(C{sg * v[k].x + p.x, sg * v[k].y + p.y}, wp);
         }
     }
 }
@@ -194,13 +199,17 @@ __device__ __forceinline__ void wfft_inv(C (&v)[WShape<M>::R], const WTw<M, C> &
     using S = WShape<M>;
 #pragma unroll 1
     for (int h = 1; h < S::LW; h <<= 1) {
+        // lower lane: u = v conj(W), result p - u; upper lane: u = v, result u + p
+        using R = decltype(C{}.x);
         const bool low = (t & h) != 0;
         const C ws = w.w32s[(t & (h - 1)) * (16 / h)];
+        const C wc = low ? C{ws.x, -ws.y} : C{R(1), R(0)};
+        const R sg = low ? R(-1) : R(1);
 #pragma unroll
         for (int k = 0; k < S::R; ++k) {
-            if (low) v[k] = c_mulc(v[k], ws);
-            const C p = shfl_xor_c(v[k], h);
-            v[k] = low ? c_sub(p, v[k]) : c_add(v[k], p);
+            const C u = c_mul(v[k], wc);
+            const C p = shfl_xor_c(u, h);
+            v[k] = C{sg * u.x + p.x, sg * u.y + p.y};
         }
     }
 #pragma unroll
