@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "passes"])
+    ap.add_argument("--no-workloads", action="store_true", help="skip the 32-grid and 512-grid workloads")
     return ap.parse_args()
 
 
@@ -181,6 +182,72 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------
+# secondary workloads (same protocol, reported inside the main line)
+# ----------------------------------------------------------------------------
+def measure_workload(safr, synth, torch, dev, stream, k, steps, warmup, flush_l2, hbm):
+    """frames/s, p50/p99 latency and error against the FP64 oracle for workload k:
+    1 = 32 grid, 3 NGS, 3 layers, FP64 (every output compared); 3 = 512 grid, 3 NGS,
+    35 layers, FP16 storage (96 sampled outputs computed one by one by the oracle)."""
+    import oracle
+    g = synth.config(k)
+    prec = g["precision"]
+    x = synth.frame(g, seed=200 + k)
+    plan = safr.Plan(g, device=dev.index)
+    info = plan.info
+    if prec == "fp16":
+        h, sc = synth.to_fp16_storage(x)
+        xin = torch.from_numpy(h).to(dev)
+        isc = torch.from_numpy(sc).to(dev)
+        osc = torch.empty(info["L"], dtype=torch.float32, device=dev)
+        x_or = synth.from_fp16_storage(h, sc)
+    else:
+        xin = torch.from_numpy(x.astype(np.float64 if prec == "fp64" else np.float32)).to(dev)
+        isc, osc, x_or = None, None, x
+    layers = plan.empty_layers()
+
+    def one(i):
+        flush_l2(i)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        safr.safr_reconstruct(plan.handle, xin, layers, in_scales=isc, out_scales=osc, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e)
+
+    for i in range(warmup):
+        one(i)
+    lat = sorted(one(i) for i in range(steps))
+    got = layers.double().cpu().numpy()
+    if osc is not None:
+        got = got * osc.double().cpu().numpy()[:, None, None]
+    orc = oracle.OraclePlan(g)
+    if k == 1:
+        ref = orc.reconstruct(x_or)
+        err, what = float(np.linalg.norm(got - ref) / np.linalg.norm(ref)), "all outputs"
+    else:
+        rng = np.random.default_rng(7)
+        lpq = np.stack([rng.integers(0, info["L"], 96), rng.integers(0, info["M"], 96),
+                        rng.integers(0, info["M"], 96)], 1)
+        ref = orc.reconstruct_samples(x_or, lpq)
+        gs = got[lpq[:, 0], lpq[:, 1], lpq[:, 2]]
+        err, what = float(np.linalg.norm(gs - ref) / np.linalg.norm(ref)), "96 sampled outputs"
+    es = {"fp64": 8, "fp32": 4, "fp16": 2}[prec]
+    M = info["M"]
+    fbytes = (M * (M // 2) * info["L"] * info["G"] * (16 if prec == "fp64" else 8)
+              + info["G"] * info["P"] ** 2 * es + info["L"] * M * M * es)
+    mean_ms = float(np.mean(lat))
+    out = {"grid": M, "pupil": info["P"], "stars": info["G"], "layers": info["L"], "precision": prec,
+           "frames_per_s": 1e3 / mean_ms, "latency_ms": {"p50": lat[len(lat) // 2],
+                                                         "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+           "path": "fused" if safr.safr_launches_per_frame(plan.handle) == 1 else "passes",
+           "algorithmic_bytes": fbytes, "frac_of_hbm": fbytes / (mean_ms * 1e-3) / 1e9 / hbm,
+           "rel_l2_vs_oracle": err, "compared": what, "steps": steps}
+    plan.close()
+    return g["name"], out
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_safr(args):
@@ -301,6 +368,19 @@ def run_safr(args):
         got = layers.double().cpu().numpy()
         rel_l2 = float(np.linalg.norm(got - ref_layers[fi]) / np.linalg.norm(ref_layers[fi]))
 
+    workloads = {}
+    if rank == 0 and world == 1 and not args.no_workloads:
+        hbm_pk = 6800.0
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                hbm_pk = float(json.load(f).get("hbm_gbs", 6800.0))
+        except (OSError, ValueError):
+            pass
+        for kk in (1, 3):
+            name, res = measure_workload(safr, synth, torch, dev, stream, kk, min(args.steps, 100), 5, flush_l2,
+                                         hbm_pk)
+            workloads[name] = res
+
     if rank == 0:
         ph = np.array(phases)  # [steps][launches]
         ph_mean = ph.mean(axis=0).tolist()
@@ -360,6 +440,8 @@ def run_safr(args):
                     "ms_per_step": e2e_ms / args.steps},
             "wall_s_timed_region": wall,
         }
+        if workloads:
+            line["workloads"] = workloads
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
