@@ -122,6 +122,9 @@ typedef struct {
     size_t out_bytes;       /* bytes of one frame of layers                       */
     int warnings;           /* SAFR_WARN_* bits                                   */
     int precomputed;        /* 1 after safr_precompute                            */
+    int path;               /* schedule safr_reconstruct uses: SAFR_PATH_FUSED or SAFR_PATH_PASSES */
+    int tile_rows;          /* output rows per phase-3 item of the persistent kernel */
+    int autotuned;          /* 1 after safr_autotune                              */
 } safr_plan_info;
 
 /*
@@ -294,6 +297,54 @@ safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s)
 safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, int L, int G, const void *d_B,
                                      const float *d_wavefronts, float *d_layers, int *d_status,
                                      cudaStream_t stream);
+
+/*
+ * Schedule autotuner (the paper has no counterpart; its algorithm fixes no
+ * kernel schedule).  Times every candidate schedule of the plan on `stream`:
+ * the persistent kernel with each feasible phase-3 tile height (output rows
+ * per item), and the three-pass schedule.  Keeps the fastest (read back by
+ * safr_get_plan_info: path, tile_rows).  The result is cached for the process
+ * per device and plan shape (M, P, L, stars per group, precision, removeTT,
+ * resample), so later plans of the same shape are not timed again.  A set-up
+ * call: it allocates timing buffers, synchronises `stream` and overwrites the
+ * plan's workspaces.  The layers it produces differ only by rounding.
+ */
+safr_status safr_autotune(safr_plan_t plan, cudaStream_t stream);
+
+/*
+ * Batched frames (the paper has no counterpart; it reconstructs one frame at
+ * a time): frame i is reconstructed by plans[i], and the plans may differ in
+ * geometry.  FP32 frames on the persistent schedule are
+ * grouped by grid size M (32..512).  Each group runs as ONE cooperative launch
+ * that processes its frames one after the other on the whole GPU, and the
+ * parameter copy and the group launches are captured into a CUDA graph that
+ * every later call replays.  The other frames (FP16 storage, FP64, three-pass
+ * schedule, other M) are launched one by one after the graph.  The layers are
+ * those safr_reconstruct gives for each frame.
+ *
+ * safr_batch_create: `plans` [n] are borrowed (they must outlive the batch,
+ * keep their schedule, and be precomputed before safr_batch_reconstruct);
+ * allocates the batch's barrier counters, page-locked and device parameter
+ * buffers (two of each, so that two calls can be in flight) and a capture
+ * stream.  Run safr_autotune on the plans before creating the batch.
+ * safr_batch_reconstruct: arrays of n device pointers, as for
+ * safr_reconstruct (d_in_scales / d_out_scales may be NULL when no plan uses
+ * FP16 storage); asynchronous on `stream`.  It waits on the host only for the
+ * call before the previous one to finish with its parameter buffer.  The first
+ * call captures the graph.  SAFR_ERR_INVALID_ARG if a plan's schedule changed
+ * since the batch was created.
+ * safr_batch_get_status: sticky device status of the batch's plans
+ * (synchronises; clears them and re-arms the batch's barriers).
+ * safr_batch_launches: kernel launches one safr_batch_reconstruct makes.
+ */
+typedef struct safr_batch_s *safr_batch_t;
+safr_status safr_batch_create(const safr_plan_t *plans, int n, safr_batch_t *out);
+safr_status safr_batch_reconstruct(safr_batch_t batch, const void *const *d_wavefronts,
+                                   const float *const *d_in_scales, void *const *d_layers,
+                                   float *const *d_out_scales, cudaStream_t stream);
+safr_status safr_batch_get_status(safr_batch_t batch);
+int safr_batch_launches(safr_batch_t batch);
+safr_status safr_batch_destroy(safr_batch_t batch);
 
 /* Free every device and host resource of the plan (synchronises its device). */
 safr_status safr_destroy(safr_plan_t plan);

@@ -537,6 +537,9 @@ safr_status safr_get_plan_info(safr_plan_t plan, safr_plan_info *info)
     info->out_bytes = plan->out_bytes;
     info->warnings = plan->warnings;
     info->precomputed = plan->precomputed;
+    info->path = safr::use_fused(plan) ? SAFR_PATH_FUSED : SAFR_PATH_PASSES;
+    info->tile_rows = plan->f2_rt3;
+    info->autotuned = plan->autotuned;
     return SAFR_OK;
 }
 

@@ -6,6 +6,30 @@
 
 namespace safr {
 
+// The dynamic shared-memory limit of a kernel is a property of the kernel, shared
+// by every plan that launches it.  Raise it once to everything the device allows
+// next to the kernel's static shared memory (never lower it: a later plan with a
+// smaller need must not break an earlier one), and report whether `need` fits.
+inline bool smem_limit_allows(const void *kernel, size_t need)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int avail = optin - (int)fa.sharedSizeBytes;
+    if (need > (size_t)avail) return false;
+    if (fa.maxDynamicSharedSizeBytes < avail &&
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

@@ -89,7 +89,7 @@ struct Frame2Params {
     const R *tt_w;             // [2][P][P]
     const C *xy_hat;           // [2][M/2][M], j in the permuted order
     R *pm;                     // [G][P][2]
-    unsigned long long *bar;   // [2] arrival count, launch epoch
+    unsigned long long *bar;   // [2] arrival count, grid barriers completed before the launch
     unsigned long long *stamps;
     int *status;
     int star_tt[SAFR_MAX_G];
@@ -158,20 +158,21 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// Grid-wide barrier number `which` (0, 1) of the cooperative launch with epoch
-// `epoch` (read by thread 0; other threads' value is not used).  bar[0] counts arrivals over the plan's lifetime: every launch adds
-// 2 * gridDim.x, so barrier `which` of epoch E is complete when the count
-// reaches (2E + which + 1) * gridDim.x.  Arrival is one release reduction (no
-// round trip); one thread per CTA polls with acquire loads until the count is
-// reached or the time limit passes.  Returns false (SAFR_ERR_TIMEOUT recorded)
-// on a timeout.
-__device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsigned long long epoch, int which,
-                                                  int *status, unsigned long long timeout_ns, int *flag,
+// Grid-wide barrier on the arrival counter bar[0], which counts arrivals over
+// the counter's lifetime (gridDim.x per barrier).  `index` is the number of grid
+// barriers completed on the counter before this one (thread 0's value counts;
+// the others' is not used), so this barrier is complete when the count reaches
+// (index + 1) * gridDim.x.  Arrival is one release reduction (no round trip);
+// one thread per CTA polls with acquire loads until the count is reached or
+// the time limit passes.  Returns false (SAFR_ERR_TIMEOUT recorded) on a
+// timeout.
+__device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsigned long long index, int *status,
+                                                  unsigned long long timeout_ns, int *flag,
                                                   unsigned long long *arrive_mark)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned long long target = (2ull * epoch + (unsigned long long)which + 1ull) * gridDim.x;
+        const unsigned long long target = (index + 1ull) * gridDim.x;
         asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
         if (arrive_mark) *arrive_mark = gtimer();
         int ok = 1;
@@ -196,8 +197,14 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsig
 // faster than 32 warps with half the registers each at M = 256).
 __host__ __device__ constexpr int frame2_threads(int) { return 512; }
 
+// One frame of Algorithm 1 on the whole grid (all CTAs call it together).
+//   bar_base   grid barriers completed on fp.bar before this frame (thread 0)
+//   bph, tph   parities of the B and table mbarriers for this frame's first waits
+//   first      the first frame of the launch: initialises the mbarriers
+// Returns false if a bounded wait gave up (status recorded); the caller then stops.
 template <int M, typename R, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R> fp)
+__device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned long long bar_base, unsigned &bph,
+                                           unsigned tph, bool first_frame)
 {
     using C = typename Frame2Params<R>::C;
     using S = WShape<M>;
@@ -248,10 +255,6 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
         if (stamp && tid == 0 && (cond)) stamp[n] = gtimer(); \
     } while (0)
     SAFR_MARK(0, true);
-    // epoch of this launch (thread 0 only; first used at grid barrier 1).  The
-    // previous launch wrote it; stream order makes that write visible, so a plain
-    // load does (an acquire load would stall thread 0 here until it lands).
-    const unsigned long long epoch = tid == 0 ? __ldcg(fp.bar + 1) : 0ull;
 
     C *Bs = (C *)(smem + fp.off_b);   // staged B column block
     C *Dp = (C *)(smem + fp.off_d);   // [G][M] column spectra (permuted j)
@@ -265,9 +268,8 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     // Each phase issues all of its global loads before it consumes any of
     // them.  The per-lane twiddles and the values this CTA needs in later
     // phases are loaded into registers here and land while phase 1 runs.
-    unsigned tma_phase = 0;
     bool tma_pending = false;
-    if (tid == 0 && fp.stage_b) mbar_init(&mbar, 1);
+    if (tid == 0 && first_frame) mbar_init(&mbar, 1);
     auto copy_b = [&](int k) {  // thread 0 only
         const C *src = fp.B + (size_t)k * colB;
         mbar_expect_tx(&mbar, colB_bytes);
@@ -288,7 +290,11 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     const bool xy_pre = fp.any_tt && b < Mh;
     const bool rs_pre = rs0 && b < fp.n3;
     if (tid == 0) {
-        mbar_init(&mbar_t, 1);
+        if (first_frame) {
+            mbar_init(&mbar_t, 1);
+        } else {  // this CTA's reads of the previous frame's tables and B are done (block barrier)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
         const unsigned cb = (unsigned)(M * sizeof(C)), ib = (unsigned)(M * 4), wb = (unsigned)(M * sizeof(R));
         mbar_expect_tx(&mbar_t, cb + (xy_pre ? 2 * cb : 0u) + (rs_pre ? ib + wb : 0u));
         tma_load_1d(twq_s, fp.twq, cb, &mbar_t);
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     // every thread waits for the tables before its first transform (no thread leaves
     // on a timeout here: the status word records it and the barriers stay balanced)
     auto tables = [&]() {
-        mbar_wait_bounded(&mbar_t, 0, fp.timeout_ns, fp.status);
+        mbar_wait_bounded(&mbar_t, tph, fp.timeout_ns, fp.status);
         tw.load(twq_s, s_w32, t);
     };
     {   // later columns of this CTA (or every column when B is not staged): into L2
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
 
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
     auto drain = [&]() {
-        if (tma_pending) mbar_wait_bounded(&mbar, tma_phase, fp.timeout_ns, fp.status);
+        if (tma_pending) mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status);
     };
 
     // ---- phase 1: row pairs ----------------------------------------------------
@@ -408,12 +414,12 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     }
     if (b == fp.skip_cta) {  // test hook: every other CTA's first barrier must time out
         drain();
-        return;
+        return false;
     }
     SAFR_MARK(5, true);
-    if (!grid_sync_bounded(fp.bar, epoch, 0, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 6 : nullptr)) {
+    if (!grid_sync_bounded(fp.bar, bar_base, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 6 : nullptr)) {
         drain();
-        return;
+        return false;
     }
     SAFR_MARK(7, true);
 
@@ -489,11 +495,11 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
             SAFR_MARK(9, k == b);
             const C *Bcol;
             if (fp.stage_b) {
-                if (tid == 0) bar_flag = mbar_wait_bounded(&mbar, tma_phase, fp.timeout_ns, fp.status) ? 1 : -1;
+                if (tid == 0) bar_flag = mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status) ? 1 : -1;
                 __syncthreads();
                 tma_pending = false;
-                tma_phase ^= 1u;
-                if (bar_flag < 0) return;  // the copy never landed: nothing in flight any more to wait for
+                bph ^= 1u;
+                if (bar_flag < 0) return false;  // the copy never landed: nothing in flight any more to wait for
                 Bcol = Bs;
             } else {
                 Bcol = fp.B + (size_t)k * colB;
@@ -572,14 +578,11 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
         }
     }
     SAFR_MARK(14, true);
-    if (!grid_sync_bounded(fp.bar, epoch, 1, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 15 : nullptr)) {
+    if (!grid_sync_bounded(fp.bar, bar_base + 1ull, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 15 : nullptr)) {
         drain();
-        return;
+        return false;
     }
     SAFR_MARK(16, true);
-    if (b == 0 && tid == 0) {  // every CTA has read this launch's epoch: open the next one
-        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(fp.bar + 1), "l"(epoch + 1ull) : "memory");
-    }
 
     // ---- phase 3: (layer, row tile) ----------------------------------------------
     {
@@ -732,6 +735,54 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     }
     SAFR_MARK(22, true);
 #undef SAFR_MARK
+    return true;
+}
+
+// Reads the barrier count of the counter at the start of a launch (thread 0).
+// The previous launch on the counter wrote it; stream order makes that write
+// visible, so a plain load does (an acquire load would stall thread 0 until it
+// lands).  After its last grid barrier, CTA 0 stores the count plus the number
+// of barriers of this launch: every CTA has read the old value by then.
+__device__ __forceinline__ unsigned long long bar_count_read(const unsigned long long *bar)
+{
+    return threadIdx.x == 0 ? __ldcg(bar + 1) : 0ull;
+}
+__device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsigned long long base, unsigned n)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(bar + 1), "l"(base + n) : "memory");
+}
+
+// One frame per launch.
+template <int M, typename R, typename TIN, typename TOUT>
+__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R> fp)
+{
+    const unsigned long long base = bar_count_read(fp.bar);
+    unsigned bph = 0;
+    if (frame_body<M, R, TIN, TOUT>(fp, base, bph, 0u, true)) bar_count_advance(fp.bar, base, 2u);
+}
+
+// Many frames of one grid size per launch (FP32): frame f's parameters are
+// fps[f] (every frame on the same barrier counter, fps[f].bar), copied into
+// shared memory before the frame runs.  The frames run one after the other
+// on the whole grid; a CTA starts the next frame's loads while others finish.
+template <int M>
+__global__ void __launch_bounds__(frame2_threads(M), 1)
+    k_frame2_batch(const Frame2Params<float> *fps, int nframes, unsigned long long *bar)
+{
+    __shared__ __align__(16) Frame2Params<float> sfp;
+    const unsigned long long base = bar_count_read(bar);
+    unsigned bph = 0, tph = 0;
+    for (int f = 0; f < nframes; ++f) {
+        __syncthreads();  // every thread is done with the previous frame's parameters
+        const int *src = (const int *)(fps + f);
+        for (int i = threadIdx.x; i < (int)(sizeof(Frame2Params<float>) / 4); i += blockDim.x)
+            ((int *)&sfp)[i] = __ldg(src + i);
+        __syncthreads();
+        if (!frame_body<M, float, float, float>(sfp, base + 2ull * f, bph, tph, f == 0)) return;
+        tph ^= 1u;
+    }
+    bar_count_advance(bar, base, 2u * (unsigned)nframes);
 }
 
 // ----------------------------------------------------------------------------
@@ -781,6 +832,7 @@ struct Frame2Host {
         long long best_cost = 0;
         int st[2] = {0, 0}, ns[2] = {0, 0};
         for (int rt = std::min(32, M); rt >= 2; rt -= 2) {
+            if (pl->f2_rt_force > 0 && rt != pl->f2_rt_force) continue;  // a tile height the autotuner picked
             int nsm_[2] = {0, 0};
             for (int gi = 0; gi < pl->ngroups; ++gi) {
                 int mx = rt;
@@ -826,10 +878,7 @@ struct Frame2Host {
             pl->f2_nsrc3[gi] = ns[gi];
         }
         pl->f2_grid = nb;
-        if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
+        if (!smem_limit_allows(kernel, total)) return false;
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, frame2_threads(M), total) != cudaSuccess ||
             occ < 1) {

@@ -100,6 +100,8 @@ struct safr_plan_s {
     int f2_st3[2] = {0, 0}, f2_nsrc3[2] = {0, 0};
     unsigned f2_off_rs = 0, f2_off_tw = 0, f2_off_b = 0, f2_off_d = 0, f2_off_s3 = 0, f2_off_xy = 0;
     size_t f2_smem = 0;
+    int f2_rt_force = 0;        // phase-3 tile rows chosen by the autotuner (0: cost model)
+    int autotuned = 0;          // 1 after safr_autotune
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
     int gmax = 16; // compile-time bound on stars per group of the column pass

@@ -399,9 +399,9 @@ static void (*cols_kernel(int gmax))(FrameParams<R>)
 template <typename K1, typename K2, typename K3>
 static cudaError_t set_smem(K1 k1, K2 k2, K3 k3, const safr_plan_s *pl)
 {
-    cudaError_t e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_k1);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_k2);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl->smem_k3);
+    const bool ok = smem_limit_allows((const void *)k1, pl->smem_k1) && smem_limit_allows((const void *)k2, pl->smem_k2) &&
+                    smem_limit_allows((const void *)k3, pl->smem_k3);
+    cudaError_t e = ok ? cudaSuccess : cudaErrorInvalidValue;
     return e;
 }
 

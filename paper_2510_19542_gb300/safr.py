@@ -35,7 +35,9 @@ _PRECISION = {"fp32": SAFR_FP32, "fp16": SAFR_FP16_STORAGE, "fp64": SAFR_FP64}
 _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_reconstruct_host",
             "safr_get_status", "safr_get_plan_info", "safr_copy_B", "safr_trace", "safr_trace_read",
             "safr_launches_per_frame", "safr_trace_phases", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
-            "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc"]
+            "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc", "safr_autotune",
+            "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
+            "safr_batch_destroy"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -58,7 +60,8 @@ class safr_plan_info(C.Structure):
     _fields_ = [("M", C.c_int), ("P", C.c_int), ("L", C.c_int), ("G", C.c_int), ("ngroups", C.c_int),
                 ("group_kind", C.c_int * 2), ("group_G", C.c_int * 2), ("b_bytes", C.c_size_t),
                 ("workspace_bytes", C.c_size_t), ("in_bytes", C.c_size_t), ("out_bytes", C.c_size_t),
-                ("warnings", C.c_int), ("precomputed", C.c_int)]
+                ("warnings", C.c_int), ("precomputed", C.c_int), ("path", C.c_int), ("tile_rows", C.c_int),
+                ("autotuned", C.c_int)]
 
 
 _lib = None
@@ -96,6 +99,12 @@ def load(build_if_missing: bool = True):
     lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
     lib.safr_destroy.argtypes = [vp]
     lib.safr_reconstruct_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp]
+    lib.safr_autotune.argtypes = [vp, vp]
+    lib.safr_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(vp)]
+    lib.safr_batch_reconstruct.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
+    lib.safr_batch_get_status.argtypes = [vp]
+    lib.safr_batch_launches.argtypes = [vp]
+    lib.safr_batch_destroy.argtypes = [vp]
     lib.safr_status_string.argtypes = [C.c_int]
     lib.safr_status_string.restype = C.c_char_p
     for name in _EXPORTS:
@@ -253,6 +262,45 @@ def safr_reconstruct_noalloc(cuda_device: int, M: int, P: int, L: int, G: int, B
     _check(load().safr_reconstruct_noalloc(int(cuda_device), int(M), int(P), int(L), int(G), _ptr(B),
                                            _ptr(wavefronts), _ptr(layers), _ptr(status), _stream(stream)),
            "safr_reconstruct_noalloc")
+
+
+def safr_autotune(plan: int, stream=None):
+    _check(load().safr_autotune(plan, _stream(stream)), "safr_autotune")
+
+
+def _ptr_array(xs):
+    if xs is None:
+        return None
+    arr = (C.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def safr_batch_create(plans) -> int:
+    """Batch over plan handles (ints); returns the batch handle."""
+    arr = (C.c_void_p * len(plans))(*plans)
+    out = C.c_void_p()
+    _check(load().safr_batch_create(arr, len(plans), C.byref(out)), "safr_batch_create")
+    return out.value
+
+
+def safr_batch_reconstruct(batch: int, wavefronts, layers, in_scales=None, out_scales=None, stream=None):
+    """Lists of per-frame device buffers (tensors or pointers)."""
+    _check(load().safr_batch_reconstruct(batch, _ptr_array(wavefronts), _ptr_array(in_scales), _ptr_array(layers),
+                                         _ptr_array(out_scales), _stream(stream)), "safr_batch_reconstruct")
+
+
+def safr_batch_get_status(batch: int) -> int:
+    return load().safr_batch_get_status(batch)
+
+
+def safr_batch_launches(batch: int) -> int:
+    return load().safr_batch_launches(batch)
+
+
+def safr_batch_destroy(batch: int):
+    _check(load().safr_batch_destroy(batch), "safr_batch_destroy")
 
 
 def safr_destroy(plan: int):

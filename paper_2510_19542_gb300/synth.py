@@ -183,3 +183,31 @@ def to_fp16_storage(x: np.ndarray):
 
 def from_fp16_storage(h: np.ndarray, scales: np.ndarray) -> np.ndarray:
     return h.astype(np.float64) * scales.astype(np.float64)[:, None, None]
+
+
+def batch_configs(n: int = 64, seed: int = 4, grids=(128, 256, 512)) -> list:
+    """Geometries of the batched workload: n frames of uneven geometry drawn from
+    ``seed``.  Per frame: grid M from ``grids``, P = ceil(0.3125 M) pupil samples
+    across a 39 m aperture (11% obstruction), G in [3, 9] stars that are all LGS
+    (90 km, 2 arcmin ring), all NGS (1.3 arcmin ring) or a mix of both, L in
+    [3, 35] layers on 0-16 km with the exponential Cn2 profile, FP32.  Frame f's
+    inputs use seed 4000 + f."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for f in range(n):
+        M = int(rng.choice(grids))
+        G = int(rng.integers(3, 10))
+        L = int(rng.integers(3, 36))
+        mix = int(rng.integers(0, 3))  # 0 LGS only, 1 NGS only, 2 mixed
+        n_lgs = G if mix == 0 else (0 if mix == 1 else int(rng.integers(1, G)))
+        n_ngs = G - n_lgs
+        P = int(math.ceil(0.3125 * M))
+        lx, ly = _ring(2.0, [360.0 * i / max(n_lgs, 1) for i in range(n_lgs)])
+        nx, ny = _ring(1.3, [60.0 + 360.0 * i / max(n_ngs, 1) for i in range(n_ngs)])
+        h = np.linspace(0.0, 16000.0, L)
+        out.append(dict(name=f"batch-{f}", M=M, P=P, pitch=39.0 / P, diameter=39.0, obstruction=0.11,
+                        h=h, cn2=_exp_profile(h), dir_x=np.concatenate([lx, nx]), dir_y=np.concatenate([ly, ny]),
+                        kind=np.array([LGS] * n_lgs + [NGS] * n_ngs, np.int32), h_lgs=90e3, alpha=0.005,
+                        alpha_tt=0.01, beta=1.5, output_metric=1, remove_tt=1, precision="fp32",
+                        r0=0.157, L0=25.0, noise=0.02, seed=4000 + f))
+    return out

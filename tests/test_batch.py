@@ -1,0 +1,126 @@
+"""Batched frames and the schedule autotuner, through the C ABI.
+
+A batch must give, for every frame, exactly the layers that safr_reconstruct
+gives for that frame's plan: the grouped frames run the same kernel body in
+one launch per grid size, and the other frames go through safr_reconstruct
+itself.  The autotuner changes only the tiling of the last phase, so its
+layers agree with the untuned plan to FP32 rounding.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def test_batch_and_autotune_reject_bad_arguments_without_a_gpu():
+    from paper_2510_19542_gb300 import safr
+    lib = safr.load()
+    import ctypes as C
+    out = C.c_void_p()
+    assert lib.safr_batch_create(None, 3, C.byref(out)) == safr.SAFR_ERR_INVALID_ARG
+    arr = (C.c_void_p * 1)(None)
+    assert lib.safr_batch_create(arr, 1, C.byref(out)) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_batch_create(arr, 0, C.byref(out)) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_autotune(None, None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_batch_reconstruct(None, None, None, None, None, None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_batch_destroy(None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_batch_launches(None) == 0
+
+
+def _geometries(synth):
+    base = synth.scaled(synth.config(2), M=64, P=20)
+    lgs = [i for i in range(9) if base["kind"][i] == 1]
+    return [
+        ("mixed-64", base),
+        ("ngs-32", dict(synth.config(1), precision="fp32")),
+        ("lgs-64-native", dict(base, dir_x=base["dir_x"][lgs], dir_y=base["dir_y"][lgs], kind=base["kind"][lgs],
+                               output_metric=0)),
+        ("mixed-128-L5", synth.scaled(synth.config(2), M=128, P=41, L=5)),
+        ("mixed-64-again", synth.scaled(synth.config(2), M=64, P=21)),
+        ("ngs-32-fp64", synth.config(1)),                       # FP64: launched on its own
+        ("mixed-64-passes", synth.scaled(synth.config(2), M=64, P=20)),  # three-pass schedule: on its own
+        ("mixed-16", synth.scaled(synth.config(2), M=16, P=6)),  # no batch instance for M = 16
+    ]
+
+
+@pytest.mark.gpu
+def test_batch_equals_frame_by_frame():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr, synth
+    dev = torch.device("cuda:0")
+    geoms = _geometries(synth)
+    plans = []
+    for name, g in geoms:
+        p = safr.Plan(g, device=0)
+        if name.endswith("passes"):
+            safr.safr_set_path(p.handle, safr.SAFR_PATH_PASSES)
+        plans.append(p)
+    batch = safr.safr_batch_create([p.handle for p in plans])
+    grouped_m = {g["M"] for (name, g) in geoms if g.get("precision", "fp32") == "fp32"
+                 and not name.endswith("passes") and g["M"] >= 32}
+    assert safr.safr_batch_launches(batch) == len(grouped_m) + 1 + 3 + 1  # groups, FP64 fused, passes, M = 16
+    dts = {"fp32": torch.float32, "fp64": torch.float64}
+    for call, seed0 in enumerate((31, 57)):  # the first call captures the graph, the second replays it
+        xs = [torch.from_numpy(synth.random_frame(g, seed0 + i)).to(dev, dts[g.get("precision", "fp32")])
+              for i, (_, g) in enumerate(geoms)]
+        outs = [p.empty_layers().fill_(float("nan")) for p in plans]
+        safr.safr_batch_reconstruct(batch, xs, outs)
+        torch.cuda.synchronize(dev)
+        assert safr.safr_batch_get_status(batch) == 0
+        for (name, g), p, x, out in zip(geoms, plans, xs, outs):
+            ref = p.reconstruct(x)
+            torch.cuda.synchronize(dev)
+            assert torch.equal(out, ref), (call, name)
+    safr.safr_batch_destroy(batch)
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.gpu
+def test_batch_frame_against_oracle(oracle_mod):
+    """One batched frame of the seeded uneven-geometry workload (scaled down) against the FP64 oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr, synth
+    dev = torch.device("cuda:0")
+    geoms = synth.batch_configs(n=6, seed=4, grids=(32, 64))
+    plans = [safr.Plan(g, device=0) for g in geoms]
+    batch = safr.safr_batch_create([p.handle for p in plans])
+    xs_np = [synth.frame(g) for g in geoms]
+    xs = [torch.from_numpy(x.astype(np.float32)).to(dev) for x in xs_np]
+    outs = [p.empty_layers() for p in plans]
+    safr.safr_batch_reconstruct(batch, xs, outs)
+    torch.cuda.synchronize(dev)
+    assert safr.safr_batch_get_status(batch) == 0
+    for g, x, out in zip(geoms, xs_np, outs):
+        ref = oracle_mod.OraclePlan(g).reconstruct(x)
+        got = out.double().cpu().numpy()
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5, g["name"]
+    safr.safr_batch_destroy(batch)
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.gpu
+def test_autotune_keeps_the_layers_and_caches_by_shape():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr, synth
+    dev = torch.device("cuda:0")
+    g = synth.scaled(synth.config(2), M=128, P=40)
+    x = torch.from_numpy(synth.frame(g).astype(np.float32)).to(dev)
+    p = safr.Plan(g, device=0)
+    before = p.reconstruct(x).double().cpu().numpy()
+    safr.safr_autotune(p.handle)
+    info = safr.safr_get_plan_info(p.handle)
+    assert info["autotuned"] == 1 and info["path"] in (safr.SAFR_PATH_FUSED, safr.SAFR_PATH_PASSES)
+    after = p.reconstruct(x).double().cpu().numpy()
+    assert np.linalg.norm(after - before) / np.linalg.norm(before) <= 2e-6
+    assert safr.safr_get_status(p.handle) == 0
+    q = safr.Plan(g, device=0)  # same shape: the cached schedule, no timing
+    safr.safr_autotune(q.handle)
+    iq = safr.safr_get_plan_info(q.handle)
+    assert (iq["path"], iq["tile_rows"], iq["autotuned"]) == (info["path"], info["tile_rows"], 1)
+    p.close()
+    q.close()

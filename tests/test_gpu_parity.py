@@ -284,3 +284,25 @@ def test_grid_barrier_timeout_is_reported_not_hung(safr, synth):
     assert safr.safr_get_status(plan.handle) == 0
     assert torch.equal(again, good)
     plan.close()
+
+
+def test_plans_created_later_do_not_break_earlier_ones(safr, synth):
+    """A kernel's shared-memory limit is shared by every plan that launches it: a
+    plan with a smaller need, created later, must not make an earlier plan's
+    launch fail (both schedules)."""
+    big_g = synth.scaled(synth.config(2), M=128, P=41)
+    small_g = synth.scaled(synth.config(2), M=16, P=6)
+    for path in (1, 2):
+        big = safr.Plan(big_g, device=0, path=path)
+        x = torch.from_numpy(synth.random_frame(big_g, 2).astype(np.float32)).cuda()
+        ref = big.reconstruct(x).clone()
+        small = safr.Plan(small_g, device=0, path=path)
+        small.reconstruct(torch.zeros((9, 6, 6), device="cuda"))
+        again = big.reconstruct(x)
+        torch.cuda.synchronize()
+        assert torch.equal(again, ref)
+        big_same_m = safr.Plan(synth.scaled(synth.config(2), M=128, P=12, L=3), device=0, path=path)
+        big_same_m.reconstruct(torch.zeros((9, 12, 12), device="cuda"))
+        assert torch.equal(big.reconstruct(x), ref)
+        for p in (big, small, big_same_m):
+            p.close()
