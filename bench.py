@@ -247,6 +247,70 @@ def measure_workload(safr, synth, torch, dev, stream, k, steps, warmup, flush_l2
     return g["name"], out
 
 
+def measure_batch(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm, n=64):
+    """The batched workload: n frames of uneven geometry (seeded), one plan per
+    frame, autotuned, reconstructed by one safr_batch_reconstruct per step (one
+    CUDA graph launch of the frames' own launches).  Beside it, the same frames
+    submitted one by one through safr_reconstruct."""
+    geoms = synth.batch_configs(n=n, seed=4)
+    plans = [safr.Plan(g, device=dev.index) for g in geoms]
+    for p in plans:
+        safr.safr_autotune(p.handle, stream)
+    xs = [torch.from_numpy(synth.random_frame(g, 4000 + f).astype(np.float32)).to(dev) for f, g in enumerate(geoms)]
+    outs = [p.empty_layers() for p in plans]
+    batch = safr.safr_batch_create([p.handle for p in plans])
+
+    def timed(fn, i):
+        flush_l2(i)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e)
+
+    run_batch = lambda: safr.safr_batch_reconstruct(batch, xs, outs, stream=stream)  # noqa: E731
+
+    def run_seq():
+        for p, x, o in zip(plans, xs, outs):
+            safr.safr_reconstruct(p.handle, x, o, stream=stream)
+
+    for i in range(warmup):
+        timed(run_batch, i)
+        timed(run_seq, i)
+    tb = [timed(run_batch, i) for i in range(steps)]
+    ts = [timed(run_seq, i) for i in range(steps)]
+    # every frame of the batch equals its frame-by-frame result
+    run_batch()
+    torch.cuda.synchronize(dev)
+    got = [o.clone() for o in outs]
+    run_seq()
+    torch.cuda.synchronize(dev)
+    same = all(torch.equal(a, b) for a, b in zip(got, outs))
+    status = safr.safr_batch_get_status(batch)
+    nbytes = 0
+    for p in plans:
+        i = p.info
+        M = i["M"]
+        nbytes += M * (M // 2) * i["L"] * i["G"] * 8 + i["G"] * i["P"] ** 2 * 4 + i["L"] * M * M * 4
+    paths = [safr.safr_get_plan_info(p.handle)["path"] for p in plans]
+    mb, ms = float(np.mean(tb)), float(np.mean(ts))
+    out = {"frames": n, "grids": sorted({g["M"] for g in geoms}), "stars": [3, 9], "layers": [3, 35],
+           "precision": "fp32", "frames_per_s": n / (mb * 1e-3), "ms_per_batch": mb,
+           "launches_per_batch": safr.safr_batch_launches(batch), "graph": safr.safr_batch_graph(batch),
+           "autotuned_paths": {
+               "fused": paths.count(safr.SAFR_PATH_FUSED), "passes": paths.count(safr.SAFR_PATH_PASSES)},
+           "algorithmic_bytes_per_batch": nbytes, "frac_of_hbm": nbytes / (mb * 1e-3) / 1e9 / hbm,
+           "one_by_one": {"frames_per_s": n / (ms * 1e-3), "ms_per_batch": ms},
+           "equals_frame_by_frame": bool(same), "device_status": status, "steps": steps,
+           "l2": "flushed before every timed batch"}
+    safr.safr_batch_destroy(batch)
+    for p in plans:
+        p.close()
+    return "batched-64-uneven", out
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -380,6 +444,8 @@ def run_safr(args):
             name, res = measure_workload(safr, synth, torch, dev, stream, kk, min(args.steps, 100), 5, flush_l2,
                                          hbm_pk)
             workloads[name] = res
+        name, res = measure_batch(safr, synth, torch, dev, stream, min(args.steps, 20), 3, flush_l2, hbm_pk)
+        workloads[name] = res
 
     if rank == 0:
         ph = np.array(phases)  # [steps][launches]

@@ -314,28 +314,27 @@ safr_status safr_autotune(safr_plan_t plan, cudaStream_t stream);
 /*
  * Batched frames (the paper has no counterpart; it reconstructs one frame at
  * a time): frame i is reconstructed by plans[i], and the plans may differ in
- * geometry.  FP32 frames on the persistent schedule are
- * grouped by grid size M (32..512).  Each group runs as ONE cooperative launch
- * that processes its frames one after the other on the whole GPU, and the
- * parameter copy and the group launches are captured into a CUDA graph that
- * every later call replays.  The other frames (FP16 storage, FP64, three-pass
- * schedule, other M) are launched one by one after the graph.  The layers are
- * those safr_reconstruct gives for each frame.
+ * geometry, precision and schedule.  Every frame's launches (its persistent
+ * kernel, or its three passes) are captured once into ONE CUDA graph, and each
+ * call replays it with a single graph launch, so the frames run back to back
+ * with no host submission between them.  The graph holds the frames' buffer
+ * pointers and schedules: a call with other pointers, or after a plan's
+ * schedule changed (safr_autotune, safr_set_path), captures it again.  If a
+ * capture fails the frames are launched one by one on the stream.  The layers
+ * are exactly those of safr_reconstruct for each frame.
  *
  * safr_batch_create: `plans` [n] are borrowed (they must outlive the batch,
- * keep their schedule, and be precomputed before safr_batch_reconstruct);
- * allocates the batch's barrier counters, page-locked and device parameter
- * buffers (two of each, so that two calls can be in flight) and a capture
- * stream.  Run safr_autotune on the plans before creating the batch.
- * safr_batch_reconstruct: arrays of n device pointers, as for
- * safr_reconstruct (d_in_scales / d_out_scales may be NULL when no plan uses
- * FP16 storage); asynchronous on `stream`.  It waits on the host only for the
- * call before the previous one to finish with its parameter buffer.  The first
- * call captures the graph.  SAFR_ERR_INVALID_ARG if a plan's schedule changed
- * since the batch was created.
+ * be precomputed before safr_batch_reconstruct, and not be reconstructed
+ * concurrently on another stream, since the frames use their plans'
+ * workspaces); allocates a capture stream.
+ * safr_batch_reconstruct: arrays of n pointers, as for safr_reconstruct
+ * (d_in_scales / d_out_scales may be NULL when no plan uses FP16 storage);
+ * asynchronous on `stream`, no host synchronisation.  A capture (first call,
+ * new pointers) makes the call slower on the host.
  * safr_batch_get_status: sticky device status of the batch's plans
- * (synchronises; clears them and re-arms the batch's barriers).
+ * (synchronises and clears them, as safr_get_status).
  * safr_batch_launches: kernel launches one safr_batch_reconstruct makes.
+ * safr_batch_graph: 1 if the last call ran as a graph launch.
  */
 typedef struct safr_batch_s *safr_batch_t;
 safr_status safr_batch_create(const safr_plan_t *plans, int n, safr_batch_t *out);
@@ -344,6 +343,7 @@ safr_status safr_batch_reconstruct(safr_batch_t batch, const void *const *d_wave
                                    float *const *d_out_scales, cudaStream_t stream);
 safr_status safr_batch_get_status(safr_batch_t batch);
 int safr_batch_launches(safr_batch_t batch);
+int safr_batch_graph(safr_batch_t batch);
 safr_status safr_batch_destroy(safr_batch_t batch);
 
 /* Free every device and host resource of the plan (synchronises its device). */

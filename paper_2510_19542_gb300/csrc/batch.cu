@@ -1,69 +1,35 @@
 // Batched frames and the schedule autotuner.
 //
 // safr_batch_*: n frames, frame i reconstructed by plans[i] (plans may differ in
-// geometry).  FP32 frames whose plan runs the persistent kernel are grouped by
-// grid size M; each group is ONE persistent cooperative launch that runs its
-// frames one after the other on the whole grid (k_frame2_batch), so a CTA
-// starts the next frame's loads while others finish the last one and there is
-// no launch gap between frames.  The parameter copy and the group launches are
-// captured once into a CUDA graph and replayed by every later call.  Frames of
-// other plans (FP16 storage, FP64, the three-pass schedule) are launched on
-// the stream after the graph.
+// geometry, precision and schedule).  Every frame's launches (one persistent
+// cooperative kernel, or the three passes) are captured into ONE CUDA graph;
+// each call replays it with a single graph launch.  The graph bakes in the
+// frames' buffer pointers, so a call with other pointers captures it again.
+//
+// A single persistent launch that loops over a device array of frame
+// parameters was built and measured slower than this graph (4.49 ms against
+// 3.83 ms per batch of the 64-frame uneven workload): its frame parameters
+// come from memory instead of the constant bank that holds kernel arguments,
+// which costs registers (spills at M = 512) and load latency in every phase.
 //
 // safr_autotune: times the candidate schedules of a plan (persistent kernel
 // with each feasible phase-3 tile height, and the three-pass schedule) on the
-// plan's own device buffers and keeps the fastest; results are cached per
-// plan shape and device, so plans of the same shape are tuned once.
+// plan's own device and keeps the fastest; results are cached per plan shape
+// and device, so plans of the same shape are tuned once.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
-#include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
 #include <tuple>
 #include <vector>
 
-#include "frame_impl.cuh"
 #include "plan.h"
 #include "safr.h"
 
-namespace safr {
-bool frame2_configure_f32(safr_plan_s *pl, int nsm);
-bool configure_fused(safr_plan_s *pl);
-cudaError_t launch_fused(safr_plan_s *pl, const void *in, const float *in_scales, void *out, float *out_scales,
-                         cudaStream_t stream);
-}  // namespace safr
-
 namespace {
-
-using safr::Frame2Params;
-
-// grid sizes with a batch kernel instance (FP32)
-template <int M>
-struct BatchInst {
-    static void *kernel() { return (void *)safr::k_frame2_batch<M>; }
-    static Frame2Params<float> params(safr_plan_s *pl, const void *in, void *out)
-    {
-        return safr::Frame2Host<M, float>::params(pl, in, nullptr, out, nullptr);
-    }
-};
-
-template <typename F>
-bool with_batch_m(int M, F &&f)
-{
-    switch (M) {
-    case 32: f(BatchInst<32>{}); return true;
-    case 64: f(BatchInst<64>{}); return true;
-    case 128: f(BatchInst<128>{}); return true;
-    case 256: f(BatchInst<256>{}); return true;
-    case 512: f(BatchInst<512>{}); return true;
-    default: return false;
-    }
-}
-
-bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // ---------------------------------------------------------------------------
 // autotune cache: plan shape and device -> (path, phase-3 tile rows)
@@ -81,36 +47,6 @@ TuneKey tune_key(const safr_plan_s *pl)
     return TuneKey(pl->device, nsm, pl->M, pl->P, pl->L, g0, g1, pl->precision, pl->remove_tt, rs, pl->ngroups);
 }
 
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// batch object
-// ---------------------------------------------------------------------------
-struct safr_batch_s {
-    struct Group {
-        int M = 0;
-        void *kernel = nullptr;
-        std::vector<int> frames;  // indices into the batch
-        size_t smem = 0;
-        size_t first = 0;         // first parameter slot of the group
-        unsigned long long *d_bar = nullptr;
-    };
-    int device = 0, n = 0, grid = 0;
-    std::vector<safr_plan_s *> plans;
-    std::vector<Group> groups;
-    std::vector<int> loose;  // frames launched one by one through safr_reconstruct
-    size_t nslots = 0;
-    Frame2Params<float> *h_params[2] = {nullptr, nullptr};  // page-locked
-    Frame2Params<float> *d_params[2] = {nullptr, nullptr};
-    cudaEvent_t done[2] = {nullptr, nullptr};
-    cudaGraphExec_t exec[2] = {nullptr, nullptr};
-    bool tried[2] = {false, false};
-    cudaStream_t cap = nullptr;
-    unsigned long long calls = 0;
-};
-
-namespace {
-
 struct BatchDeviceGuard {
     int prev = -1;
     bool ok = false;
@@ -126,66 +62,59 @@ struct BatchDeviceGuard {
     }
 };
 
-void batch_free(safr_batch_s *b)
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// batch object
+// ---------------------------------------------------------------------------
+struct safr_batch_s {
+    int device = 0, n = 0;
+    std::vector<safr_plan_s *> plans;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_failed = false;
+    std::vector<const void *> key;  // buffer pointers and schedules the graph was captured with
+    cudaStream_t cap = nullptr;
+};
+
+namespace {
+
+// the frames' launches on `st`, in order
+safr_status enqueue_frames(safr_batch_s *b, const void *const *in, const float *const *isc, void *const *out,
+                           float *const *osc, cudaStream_t st)
 {
-    for (auto &g : b->groups)
-        if (g.d_bar) cudaFree(g.d_bar);
-    for (int c = 0; c < 2; ++c) {
-        if (b->h_params[c]) cudaFreeHost(b->h_params[c]);
-        if (b->d_params[c]) cudaFree(b->d_params[c]);
-        if (b->done[c]) cudaEventDestroy(b->done[c]);
-        if (b->exec[c]) cudaGraphExecDestroy(b->exec[c]);
+    for (int i = 0; i < b->n; ++i) {
+        const safr_status s =
+            safr_reconstruct(b->plans[i], in[i], isc ? isc[i] : nullptr, out[i], osc ? osc[i] : nullptr, st);
+        if (s != SAFR_OK) return s;
     }
-    if (b->cap) cudaStreamDestroy(b->cap);
+    return SAFR_OK;
 }
 
-// One cooperative launch of a group's batch kernel on `st`.
-cudaError_t launch_group(const safr_batch_s *b, const safr_batch_s::Group &g, int c, cudaStream_t st)
+// Capture the frames' launches into a graph (trace events left out).
+void capture(safr_batch_s *b, const void *const *in, const float *const *isc, void *const *out, float *const *osc)
 {
-    const Frame2Params<float> *dp = b->d_params[c] + g.first;
-    int nfr = (int)g.frames.size();
-    unsigned long long *bar = g.d_bar;
-    void *args[] = {(void *)&dp, (void *)&nfr, (void *)&bar};
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(b->grid);
-    cfg.blockDim = dim3(safr::frame2_threads(g.M));
-    cfg.dynamicSmemBytes = g.smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelExC(&cfg, g.kernel, args);
-}
-
-// parameter copy + group launches, on `st`
-cudaError_t enqueue_groups(const safr_batch_s *b, int c, cudaStream_t st)
-{
-    cudaError_t e = cudaMemcpyAsync(b->d_params[c], b->h_params[c], b->nslots * sizeof(Frame2Params<float>),
-                                    cudaMemcpyHostToDevice, st);
-    for (const auto &g : b->groups)
-        if (e == cudaSuccess) e = launch_group(b, g, c, st);
-    return e;
-}
-
-// Capture the copy and the group launches of parameter buffer c into a graph.
-void capture(safr_batch_s *b, int c)
-{
-    b->tried[c] = true;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_failed = true;
+    std::vector<int> trace(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        trace[i] = b->plans[i]->trace;
+        b->plans[i]->trace = 0;
+    }
     cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        cudaGetLastError();
-        return;
+    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        const safr_status s = enqueue_frames(b, in, isc, out, osc, b->cap);
+        const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+        if (s == SAFR_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess)
+            b->graph_failed = false;
+        else
+            b->exec = nullptr;
+        if (graph) cudaGraphDestroy(graph);
     }
-    const cudaError_t e = enqueue_groups(b, c, b->cap);
-    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-    if (e != cudaSuccess || e2 != cudaSuccess || !graph ||
-        cudaGraphInstantiate(&b->exec[c], graph, 0) != cudaSuccess) {
-        b->exec[c] = nullptr;
-        cudaGetLastError();
-    }
-    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    for (int i = 0; i < b->n; ++i) b->plans[i]->trace = trace[i];
 }
 
 }  // namespace
@@ -206,58 +135,11 @@ safr_status safr_batch_create(const safr_plan_t *plans, int n, safr_batch_t *out
     b->device = plans[0]->device;
     b->n = n;
     b->plans.assign(plans, plans + n);
-    auto fail = [&](safr_status s) {
-        batch_free(b);
-        delete b;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
-        return s;
-    };
-    // FP32 frames on the persistent kernel, grouped by grid size; the rest go one by one
-    for (int i = 0; i < n; ++i) {
-        safr_plan_s *pl = plans[i];
-        bool grouped = false;
-        if (pl->precision == SAFR_FP32 && safr::use_fused(pl)) {
-            with_batch_m(pl->M, [&](auto inst) {
-                using I = decltype(inst);
-                auto it = std::find_if(b->groups.begin(), b->groups.end(),
-                                       [&](const safr_batch_s::Group &g) { return g.M == pl->M; });
-                if (it == b->groups.end()) {
-                    safr_batch_s::Group g;
-                    g.M = pl->M;
-                    g.kernel = I::kernel();
-                    b->groups.push_back(g);
-                    it = b->groups.end() - 1;
-                }
-                it->frames.push_back(i);
-                it->smem = std::max(it->smem, pl->f2_smem);
-                b->grid = pl->f2_grid;
-                grouped = true;
-            });
-        }
-        if (!grouped) b->loose.push_back(i);
+        delete b;
+        return SAFR_ERR_CUDA;
     }
-    for (auto &g : b->groups) {
-        g.first = b->nslots;
-        b->nslots += g.frames.size();
-        if (!safr::smem_limit_allows(g.kernel, g.smem)) return fail(SAFR_ERR_UNSUPPORTED_SIZE);
-        int occ = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, g.kernel, safr::frame2_threads(g.M), g.smem) !=
-                cudaSuccess ||
-            occ < 1)
-            return fail(SAFR_ERR_UNSUPPORTED_SIZE);
-        if (cudaMalloc((void **)&g.d_bar, 2 * sizeof(unsigned long long)) != cudaSuccess) return fail(SAFR_ERR_OOM);
-        if (cudaMemset(g.d_bar, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return fail(SAFR_ERR_CUDA);
-    }
-    if (b->nslots > 0)
-        for (int c = 0; c < 2; ++c) {
-            if (cudaMallocHost((void **)&b->h_params[c], b->nslots * sizeof(Frame2Params<float>)) != cudaSuccess)
-                return fail(SAFR_ERR_OOM);
-            if (cudaMalloc((void **)&b->d_params[c], b->nslots * sizeof(Frame2Params<float>)) != cudaSuccess)
-                return fail(SAFR_ERR_OOM);
-        }
-    for (int c = 0; c < 2; ++c)
-        if (cudaEventCreateWithFlags(&b->done[c], cudaEventDisableTiming) != cudaSuccess) return fail(SAFR_ERR_CUDA);
-    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(SAFR_ERR_CUDA);
     *out = b;
     return SAFR_OK;
 }
@@ -266,75 +148,62 @@ safr_status safr_batch_reconstruct(safr_batch_t b, const void *const *d_wavefron
                                    void *const *d_layers, float *const *d_out_scales, cudaStream_t stream)
 {
     if (!b || !d_wavefronts || !d_layers) return SAFR_ERR_INVALID_ARG;
+    std::vector<const void *> key;
+    key.reserve((size_t)b->n * 6);
     for (int i = 0; i < b->n; ++i) {
         const safr_plan_s *pl = b->plans[i];
         if (!pl->precomputed) return SAFR_ERR_NOT_PRECOMPUTED;
         if (!d_wavefronts[i] || !d_layers[i]) return SAFR_ERR_INVALID_ARG;
         if (!aligned16(d_wavefronts[i]) || !aligned16(d_layers[i])) return SAFR_ERR_MISALIGNED;
         const bool fp16 = pl->precision == SAFR_FP16_STORAGE;
-        if (fp16 && (!d_out_scales || !d_out_scales[i])) return SAFR_ERR_INVALID_ARG;
+        const float *isc = d_in_scales ? d_in_scales[i] : nullptr;
+        float *osc = d_out_scales ? d_out_scales[i] : nullptr;
+        if (fp16 && !osc) return SAFR_ERR_INVALID_ARG;
+        if (!fp16 && (isc || osc)) return SAFR_ERR_INVALID_ARG;
+        if ((isc && !aligned16(isc)) || (osc && !aligned16(osc))) return SAFR_ERR_MISALIGNED;
+        key.push_back(d_wavefronts[i]);
+        key.push_back(isc);
+        key.push_back(d_layers[i]);
+        key.push_back(osc);
+        key.push_back((const void *)(uintptr_t)(safr::use_fused(pl) ? 1 + pl->f2_rt3 : 0));
+        key.push_back((const void *)(uintptr_t)pl->f2_smem);
     }
-    for (const auto &g : b->groups)  // schedules fixed when the batch was created (autotune first)
-        for (int i : g.frames)
-            if (!safr::use_fused(b->plans[i]) || b->plans[i]->f2_smem > g.smem) return SAFR_ERR_INVALID_ARG;
     BatchDeviceGuard guard(b->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
-    const int c = (int)(b->calls & 1u);
-    // the call that last used parameter buffer c has finished with it
-    if (b->calls >= 2 && cudaEventSynchronize(b->done[c]) != cudaSuccess) return SAFR_ERR_CUDA;
-    for (const auto &g : b->groups)
-        for (size_t s = 0; s < g.frames.size(); ++s) {
-            const int i = g.frames[s];
-            safr_plan_s *pl = b->plans[i];
-            Frame2Params<float> fp{};
-            with_batch_m(g.M, [&](auto inst) { fp = decltype(inst)::params(pl, d_wavefronts[i], d_layers[i]); });
-            fp.bar = g.d_bar;
-            fp.stamps = nullptr;
-            fp.skip_cta = -1;
-            b->h_params[c][g.first + s] = fp;
-        }
-    if (b->nslots > 0) {
-        if (!b->tried[c]) capture(b, c);
-        const cudaError_t e = b->exec[c] ? cudaGraphLaunch(b->exec[c], stream) : enqueue_groups(b, c, stream);
-        if (e != cudaSuccess) {
+    if (key != b->key) {  // other buffers or schedules: capture again
+        b->key = key;
+        capture(b, d_wavefronts, d_in_scales, d_layers, d_out_scales);
+    }
+    if (b->exec) {
+        if (cudaGraphLaunch(b->exec, stream) != cudaSuccess) {
             cudaGetLastError();
             return SAFR_ERR_CUDA;
         }
+        return SAFR_OK;
     }
-    for (int i : b->loose) {
-        const safr_status s = safr_reconstruct(b->plans[i], d_wavefronts[i], d_in_scales ? d_in_scales[i] : nullptr,
-                                               d_layers[i], d_out_scales ? d_out_scales[i] : nullptr, stream);
-        if (s != SAFR_OK) return s;
-    }
-    if (cudaEventRecord(b->done[c], stream) != cudaSuccess) return SAFR_ERR_CUDA;
-    ++b->calls;
-    return SAFR_OK;
+    return enqueue_frames(b, d_wavefronts, d_in_scales, d_layers, d_out_scales, stream);
 }
 
 safr_status safr_batch_get_status(safr_batch_t b)
 {
     if (!b) return SAFR_ERR_INVALID_ARG;
-    BatchDeviceGuard guard(b->device);
-    if (!guard.ok) return SAFR_ERR_CUDA;
     safr_status first = SAFR_OK;
     for (int i = 0; i < b->n; ++i) {
         const safr_status s = safr_get_status(b->plans[i]);
         if (first == SAFR_OK) first = s;
     }
-    if (first != SAFR_OK)  // re-arm the groups' barriers, which a timeout leaves half-counted
-        for (auto &g : b->groups)
-            if (cudaMemset(g.d_bar, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return SAFR_ERR_CUDA;
-    if (cudaDeviceSynchronize() != cudaSuccess) return SAFR_ERR_CUDA;
     return first;
 }
 
 int safr_batch_launches(safr_batch_t b)
 {
     if (!b) return 0;
-    int n = (int)b->groups.size();
-    for (int i : b->loose) n += safr_launches_per_frame(b->plans[i]);
+    int n = 0;
+    for (int i = 0; i < b->n; ++i) n += safr_launches_per_frame(b->plans[i]);
     return n;
 }
+
+int safr_batch_graph(safr_batch_t b) { return b && b->exec ? 1 : 0; }
 
 safr_status safr_batch_destroy(safr_batch_t b)
 {
@@ -342,7 +211,8 @@ safr_status safr_batch_destroy(safr_batch_t b)
     {
         BatchDeviceGuard guard(b->device);
         cudaDeviceSynchronize();
-        batch_free(b);
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->cap) cudaStreamDestroy(b->cap);
     }
     delete b;
     return SAFR_OK;

@@ -762,29 +762,6 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     if (frame_body<M, R, TIN, TOUT>(fp, base, bph, 0u, true)) bar_count_advance(fp.bar, base, 2u);
 }
 
-// Many frames of one grid size per launch (FP32): frame f's parameters are
-// fps[f] (every frame on the same barrier counter, fps[f].bar), copied into
-// shared memory before the frame runs.  The frames run one after the other
-// on the whole grid; a CTA starts the next frame's loads while others finish.
-template <int M>
-__global__ void __launch_bounds__(frame2_threads(M), 1)
-    k_frame2_batch(const Frame2Params<float> *fps, int nframes, unsigned long long *bar)
-{
-    __shared__ __align__(16) Frame2Params<float> sfp;
-    const unsigned long long base = bar_count_read(bar);
-    unsigned bph = 0, tph = 0;
-    for (int f = 0; f < nframes; ++f) {
-        __syncthreads();  // every thread is done with the previous frame's parameters
-        const int *src = (const int *)(fps + f);
-        for (int i = threadIdx.x; i < (int)(sizeof(Frame2Params<float>) / 4); i += blockDim.x)
-            ((int *)&sfp)[i] = __ldg(src + i);
-        __syncthreads();
-        if (!frame_body<M, float, float, float>(sfp, base + 2ull * f, bph, tph, f == 0)) return;
-        tph ^= 1u;
-    }
-    bar_count_advance(bar, base, 2u * (unsigned)nframes);
-}
-
 // ----------------------------------------------------------------------------
 // host side (instantiated per precision)
 // ----------------------------------------------------------------------------

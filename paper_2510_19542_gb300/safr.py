@@ -37,7 +37,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_launches_per_frame", "safr_trace_phases", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
             "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc", "safr_autotune",
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
-            "safr_batch_destroy"]
+            "safr_batch_destroy", "safr_batch_graph"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -104,6 +104,7 @@ def load(build_if_missing: bool = True):
     lib.safr_batch_reconstruct.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), vp]
     lib.safr_batch_get_status.argtypes = [vp]
     lib.safr_batch_launches.argtypes = [vp]
+    lib.safr_batch_graph.argtypes = [vp]
     lib.safr_batch_destroy.argtypes = [vp]
     lib.safr_status_string.argtypes = [C.c_int]
     lib.safr_status_string.restype = C.c_char_p
@@ -297,6 +298,10 @@ def safr_batch_get_status(batch: int) -> int:
 
 def safr_batch_launches(batch: int) -> int:
     return load().safr_batch_launches(batch)
+
+
+def safr_batch_graph(batch: int) -> int:
+    return load().safr_batch_graph(batch)
 
 
 def safr_batch_destroy(batch: int):

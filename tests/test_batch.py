@@ -1,9 +1,8 @@
 """Batched frames and the schedule autotuner, through the C ABI.
 
 A batch must give, for every frame, exactly the layers that safr_reconstruct
-gives for that frame's plan: the grouped frames run the same kernel body in
-one launch per grid size, and the other frames go through safr_reconstruct
-itself.  The autotuner changes only the tiling of the last phase, so its
+gives for that frame's plan: the batch replays a CUDA graph of the frames' own
+launches.  The autotuner changes only the tiling of the last phase, so its
 layers agree with the untuned plan to FP32 rounding.
 """
 import numpy as np
@@ -37,9 +36,9 @@ def _geometries(synth):
                                output_metric=0)),
         ("mixed-128-L5", synth.scaled(synth.config(2), M=128, P=41, L=5)),
         ("mixed-64-again", synth.scaled(synth.config(2), M=64, P=21)),
-        ("ngs-32-fp64", synth.config(1)),                       # FP64: launched on its own
-        ("mixed-64-passes", synth.scaled(synth.config(2), M=64, P=20)),  # three-pass schedule: on its own
-        ("mixed-16", synth.scaled(synth.config(2), M=16, P=6)),  # no batch instance for M = 16
+        ("ngs-32-fp64", synth.config(1)),                                # FP64
+        ("mixed-64-passes", synth.scaled(synth.config(2), M=64, P=20)),  # three-pass schedule
+        ("mixed-16", synth.scaled(synth.config(2), M=16, P=6)),
     ]
 
 
@@ -57,21 +56,27 @@ def test_batch_equals_frame_by_frame():
             safr.safr_set_path(p.handle, safr.SAFR_PATH_PASSES)
         plans.append(p)
     batch = safr.safr_batch_create([p.handle for p in plans])
-    grouped_m = {g["M"] for (name, g) in geoms if g.get("precision", "fp32") == "fp32"
-                 and not name.endswith("passes") and g["M"] >= 32}
-    assert safr.safr_batch_launches(batch) == len(grouped_m) + 1 + 3 + 1  # groups, FP64 fused, passes, M = 16
+    assert safr.safr_batch_launches(batch) == sum(safr.safr_launches_per_frame(p.handle) for p in plans)
     dts = {"fp32": torch.float32, "fp64": torch.float64}
-    for call, seed0 in enumerate((31, 57)):  # the first call captures the graph, the second replays it
+    for call, seed0 in enumerate((31, 57)):  # new buffers each call: captured again each time
         xs = [torch.from_numpy(synth.random_frame(g, seed0 + i)).to(dev, dts[g.get("precision", "fp32")])
               for i, (_, g) in enumerate(geoms)]
         outs = [p.empty_layers().fill_(float("nan")) for p in plans]
         safr.safr_batch_reconstruct(batch, xs, outs)
         torch.cuda.synchronize(dev)
         assert safr.safr_batch_get_status(batch) == 0
+        assert safr.safr_batch_graph(batch) == 1
         for (name, g), p, x, out in zip(geoms, plans, xs, outs):
             ref = p.reconstruct(x)
             torch.cuda.synchronize(dev)
             assert torch.equal(out, ref), (call, name)
+    # same buffers, new data: the captured graph is replayed
+    for x in xs:
+        x.mul_(-0.5)
+    safr.safr_batch_reconstruct(batch, xs, outs)
+    torch.cuda.synchronize(dev)
+    for (name, g), p, x, out in zip(geoms, plans, xs, outs):
+        assert torch.equal(out, p.reconstruct(x)), ("replay", name)
     safr.safr_batch_destroy(batch)
     for p in plans:
         p.close()
