@@ -346,6 +346,85 @@ int safr_batch_launches(safr_batch_t batch);
 int safr_batch_graph(safr_batch_t batch);
 safr_status safr_batch_destroy(safr_batch_t batch);
 
+/*
+ * Learned spectral filter.  Section 3.1 writes the regularised inverse as
+ * B(n) = diag(s) V g(Sigma) U^H for any regularising filter g of the singular
+ * values of A(n) = U Sigma V^H (its experiments use Tikhonov,
+ * g(s) = s / (s^2 + alpha)).  Here the filter factor phi in (0, 1) of singular
+ * direction r in layer l comes from a small MLP of four features:
+ *
+ *   x = (|n| / (M/2), h_l / 20 km, (log10 sigma_r + 4) / 4, noise level / 0.05)
+ *   phi = logistic(W3 gelu(W2 gelu(W1 gelu(W0 x + b0) + b1) + b2) + b3)
+ *   B_lg(n) = s_l(n) sum_r V_lr(n) (phi / sigma_r) conj(U_gr(n))
+ *
+ * (phi = 1 gives the pseudo-inverse, phi = sigma^2 / (sigma^2 + alpha)
+ * Tikhonov).  Hidden width 64, GELU in its exact erf form.  The parameters
+ * are BF16 on the GPU and the arithmetic FP32; the SVD of every A(n) is FP64.
+ * Parameter layout, SAFR_FILTER_PARAMS floats, row-major W[out][in]:
+ *   W0[64][4], b0[64], W1[64][64], b1[64], W2[64][64], b2[64], W3[64], b3.
+ * Only plans with one star group (no split tomography) take a learned filter
+ * (SAFR_ERR_UNSUPPORTED_SIZE otherwise), and the plan must be precomputed.
+ * The frame kernels are unchanged: only B is replaced.
+ */
+#define SAFR_FILTER_PARAMS 8705
+
+typedef struct {
+    double r0;          /* Fried parameter of the whole profile [m] of the training screens */
+    double L0;          /* outer scale [m] */
+    double noise_level; /* per-pixel noise std as a fraction of the noise-free wavefront RMS */
+    int train_frames;   /* distinct training frames (drawn again each epoch) */
+    int valid_frames;   /* held-out frames judging learned against plain SAFR */
+    int epochs;
+    double lr;          /* Adam learning rate */
+    unsigned long long seed;
+} safr_filter_config;
+
+typedef struct {
+    double train_loss_first;   /* relative squared layer error on the first training frames, initial weights */
+    double train_loss_last;    /* the same after training */
+    double valid_loss_learned; /* relative squared layer error on the held-out frames, learned filter */
+    double valid_loss_plain;   /* the same with plain SAFR's Tikhonov filter */
+    long steps;                /* Adam steps (256 frames each) */
+    int used_learned;          /* 1: B now holds the learned filter's inverse */
+    int nonfinite;             /* 1: the MLP gave a non-finite weight */
+    double noise_sd;           /* std of the real and imaginary parts of the spectral noise */
+} safr_filter_result;
+
+/*
+ * safr_filter_train: trains the MLP on the GPU.  Training frames come from
+ * the SAFR forward model in the Fourier domain, d_g(n) = sum_l
+ * exp(i theta_gl(n)) phi_l(n) + eta_g(n), with layer spectra phi_l of von
+ * Karman screens (cfg r0, L0, the plan's Cn2 weights and layer periods) and
+ * white noise eta of cfg->noise_level, drawn from Philox4x32-10 (Salmon et
+ * al., SC 2011).  Frame F takes phi_l(n), n = (j, k) with k < M/2, from the
+ * Box-Muller pair of counter (F, k M + j, l, 0) and eta_g(n) from
+ * (F, k M + j, L + g, 0); the training frames use key (seed mod 2^32,
+ * (seed >> 32) xor 0x5AFE), the held-out frames key (seed mod 2^32 + 1,
+ * (seed >> 32) xor 0x5AFE).  E|phi_l(n)|^2 = M^4 PSD_l(|n| / (2 c_l T)) /
+ * (2 (2 c_l T)^2) (half the power per complex coefficient of a real screen)
+ * and E|eta_g(n)|^2 = noise^2 E_f / M^2, E_f the expected spectral energy of
+ * one frame (a per-pixel noise std of noise x the data's RMS).  The loss is the relative squared error of the reconstructed
+ * layer spectra, minimised by Adam (FP32 master weights, BF16 copy used by
+ * the MLP) over ceil(train_frames / 256) * epochs steps of 256 frames.
+ * Held-out frames (another key) then compare the learned filter with plain
+ * SAFR: B becomes the learned filter's inverse only if its held-out error is
+ * lower and every weight it gives is finite; otherwise plain SAFR's B is
+ * rebuilt (the fallback).  weights_out [SAFR_FILTER_PARAMS] (may be NULL)
+ * receives the trained parameters rounded to BF16; res (may be NULL) the
+ * figures above.  Synchronises `stream`; allocates the filter's buffers on
+ * first use (freed with the plan).
+ *
+ * safr_filter_apply: builds B from given parameters (host, rounded to BF16)
+ * at noise level `noise_level`.  If the MLP gives a non-finite weight, plain
+ * SAFR's B is rebuilt and SAFR_ERR_DEVICE returned.  Synchronises `stream`.
+ *
+ * safr_filter_reset: rebuilds plain SAFR's B (as safr_precompute).
+ */
+safr_status safr_filter_train(safr_plan_t plan, const safr_filter_config *cfg, float *weights_out,
+                              safr_filter_result *res, cudaStream_t stream);
+safr_status safr_filter_apply(safr_plan_t plan, const float *weights, double noise_level, cudaStream_t stream);
+safr_status safr_filter_reset(safr_plan_t plan, cudaStream_t stream);
+
 /* Free every device and host resource of the plan (synchronises its device). */
 safr_status safr_destroy(safr_plan_t plan);
 

@@ -14,6 +14,11 @@ from .safr_oracle import (  # noqa: F401
     idft2,
     svd,
     group_B,
+    group_B_learned,
+    mlp_phi,
+    philox4x32_10,
+    filter_frames_loss,
+    MLP_PARAMS,
     cone,
     remove_tt,
     resample,

@@ -36,6 +36,7 @@
  */
 #include <complex.h>
 #include <math.h>
+#include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -533,5 +534,240 @@ int oracle_plan_reconstruct_samples(const oracle_plan *pl, const double *wavefro
         out[s] = total;
     }
     free(w); free(spec);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Learned spectral filter.  Section 3.1 writes the regularised inverse as     */
+/* R(A) = V g(Sigma^T) U^H for a regularising filter g of the singular values. */
+/* Here g(sigma_r) = phi / sigma_r with phi in (0, 1) from an MLP of the point */
+/* x = (|n| / (M/2), h_l / 20 km, (log10 sigma_r + 4) / 4, noise / 0.05), and */
+/* the factor may differ per layer l:                                          */
+/*   B_n[l][g] = s_l(n) sum_r V_{l r} (phi_{l r} / sigma_r) conj(U_{g r}).      */
+/* MLP: 4 -> 64 -> 64 -> 64 -> 1, GELU(z) = z (1 + erf(z / sqrt 2)) / 2 after  */
+/* each hidden layer, logistic output; parameters W0[64][4] b0[64] W1[64][64]  */
+/* b1[64] W2[64][64] b2[64] W3[64] b3, rows = outputs.                         */
+/* A singular value sigma_r <= 1e-13 sigma_max is a numerical zero (the rank of */
+/* A_n): its direction is dropped, since phi / sigma_r, unlike the Tikhonov    */
+/* factor, does not vanish as sigma_r -> 0.                                    */
+/* ------------------------------------------------------------------------- */
+#define MLP_H 64
+
+static double gelu_erf(double z) { return 0.5 * z * (1.0 + erf(z / sqrt(2.0))); }
+
+double oracle_mlp_phi(const double *p, const double *x)
+{
+    const double *W0 = p, *b0 = W0 + MLP_H * 4, *W1 = b0 + MLP_H, *b1 = W1 + MLP_H * MLP_H;
+    const double *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H, *W3 = b2 + MLP_H, *b3 = W3 + MLP_H;
+    double h1[MLP_H], h2[MLP_H], h3[MLP_H];
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b0[i];
+        for (int q = 0; q < 4; ++q) z += W0[i * 4 + q] * x[q];
+        h1[i] = gelu_erf(z);
+    }
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b1[i];
+        for (int q = 0; q < MLP_H; ++q) z += W1[i * MLP_H + q] * h1[q];
+        h2[i] = gelu_erf(z);
+    }
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b2[i];
+        for (int q = 0; q < MLP_H; ++q) z += W2[i * MLP_H + q] * h2[q];
+        h3[i] = gelu_erf(z);
+    }
+    double o = b3[0];
+    for (int q = 0; q < MLP_H; ++q) o += W3[q] * h3[q];
+    return 1.0 / (1.0 + exp(-o));
+}
+
+int oracle_group_B_learned(int M, double T, int L, const double *h, const double *c, const double *gamma, int G,
+                           const double *ax, const double *ay, double beta, const double *params,
+                           double noise_level, cplx *B)
+{
+    if (M <= 0 || M % 2 || L <= 0 || G <= 0) return -1;
+    const double omega = PI / T;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long f = 0; f < (long)M * M; ++f) {
+        int j = (int)(f / M), k = (int)(f % M);
+        cplx *Bf = B + (size_t)f * L * G;
+        for (int i = 0; i < L * G; ++i) Bf[i] = 0;
+        if (j == M / 2 || k == M / 2) continue; /* Nyquist row / column */
+        double nx = shifted_index(j, M), ny = shifted_index(k, M);
+        int R = G < L ? G : L;
+        double *s = (double *)malloc(sizeof(double) * L);
+        cplx *A = (cplx *)malloc(sizeof(cplx) * (size_t)G * L);
+        cplx *AH = (cplx *)malloc(sizeof(cplx) * (size_t)G * L);
+        cplx *Ux = (cplx *)malloc(sizeof(cplx) * (size_t)G * L);
+        cplx *Vx = (cplx *)malloc(sizeof(cplx) * (size_t)L * L);
+        cplx *U = (cplx *)malloc(sizeof(cplx) * (size_t)G * R);
+        cplx *V = (cplx *)malloc(sizeof(cplx) * (size_t)L * R);
+        double *S = (double *)malloc(sizeof(double) * L);
+        for (int l = 0; l < L; ++l) {
+            double tau = PI * PI / ((c[l] * T) * (c[l] * T));
+            s[l] = sqrt(gamma[l]) / c[l] * pow(1.0 + tau * (nx * nx + ny * ny), -beta / 2.0);
+        }
+        for (int g = 0; g < G; ++g)
+            for (int l = 0; l < L; ++l) {
+                double arg = omega * (nx * ax[g] * h[l] + ny * ay[g] * h[l]) / c[l];
+                A[g * L + l] = s[l] * (cos(arg) + I * sin(arg));
+            }
+        if (G >= L) {
+            oracle_svd(G, L, A, Ux, S, Vx);
+            for (int g = 0; g < G; ++g) for (int r = 0; r < R; ++r) U[g * R + r] = Ux[g * L + r];
+            for (int l = 0; l < L; ++l) for (int r = 0; r < R; ++r) V[l * R + r] = Vx[l * L + r];
+        } else {
+            for (int g = 0; g < G; ++g) for (int l = 0; l < L; ++l) AH[l * G + g] = conj(A[g * L + l]);
+            oracle_svd(L, G, AH, Ux, S, Vx);
+            for (int g = 0; g < G; ++g) for (int r = 0; r < R; ++r) U[g * R + r] = Vx[g * G + r];
+            for (int l = 0; l < L; ++l) for (int r = 0; r < R; ++r) V[l * R + r] = Ux[l * G + r];
+        }
+        double smax = 0;
+        for (int r = 0; r < R; ++r) smax = S[r] > smax ? S[r] : smax;
+        const double nabs = sqrt(nx * nx + ny * ny);
+        for (int l = 0; l < L; ++l)
+            for (int r = 0; r < R; ++r) {
+                if (!(S[r] > 1e-13 * smax)) continue;
+                double x[4] = {nabs / (0.5 * M), h[l] / 20e3, (log10(S[r] > 1e-12 ? S[r] : 1e-12) + 4.0) / 4.0,
+                               noise_level / 0.05};
+                double w = oracle_mlp_phi(params, x) / S[r];
+                for (int g = 0; g < G; ++g) Bf[l * G + g] += s[l] * V[l * R + r] * w * conj(U[g * R + r]);
+            }
+        free(s); free(A); free(AH); free(Ux); free(Vx); free(U); free(V); free(S);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as    */
+/* easy as 1, 2, 3", SC 2011): ten rounds; each round multiplies counter words */
+/* 0 and 2 by 0xD2511F53 and 0xCD9E8D57 (64-bit products), and the new words   */
+/* are (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the   */
+/* key is bumped by (0x9E3779B9, 0xBB67AE85) between rounds.                   */
+/* ------------------------------------------------------------------------- */
+void oracle_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out)
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3], k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0, p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1, n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Two standard normals by Box-Muller from the first two output words of    */
+/* counter (a, b, c, 0): u = (word + 1/2) 2^-32 in (0, 1).                  */
+static void normal_pair(uint32_t a, uint32_t b, uint32_t c, uint32_t k0, uint32_t k1, double *z0, double *z1)
+{
+    uint32_t ctr[4] = {a, b, c, 0u}, key[2] = {k0, k1}, o[4];
+    oracle_philox4x32_10(ctr, key, o);
+    double u1 = ((double)o[0] + 0.5) / 4294967296.0, u2 = ((double)o[1] + 0.5) / 4294967296.0;
+    double rad = sqrt(-2.0 * log(u1));
+    *z0 = rad * cos(2.0 * PI * u2);
+    *z1 = rad * sin(2.0 * PI * u2);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Training frames of the learned filter and the error of a reconstruction  */
+/* B on them.  Frames follow the layered model of Section 2 in the Fourier   */
+/* domain: the data of star g at frequency n is                              */
+/*   d_g(n) = sum_l exp(i omega n.(alpha_g h_l) / c_l) phi_l(n) + eta_g(n),   */
+/* phi_l(n) the DFT of layer l over its own M x M grid (pitch c_l delta,     */
+/* period 2 c_l T), complex normal with E|phi_l(n)|^2 =                       */
+/*   M^4 (1/2) PSD_l(|n| / (2 c_l T)) / (2 c_l T)^2,                          */
+/*   PSD_l(f) = 0.023 (r0 gamma_l^{-3/5})^{-5/3} (f^2 + L0^-2)^{-11/6}         */
+/* (von Karman; zero at n = 0), and eta_g white with E|eta|^2 =               */
+/* noise^2 E_f / M^2, E_f = sum over the full spectrum of sum_l E|phi_l|^2     */
+/* (a per-pixel noise std of noise x the data's RMS).  Frequencies k in       */
+/* [0, M/2), j in [0, M) with j != M/2 are drawn; the others follow from      */
+/* conjugate symmetry and count twice for k > 0.  Frame F draws phi_l(n) from */
+/* Philox counter (F, k M + j, l, 0) and eta_g(n) from (F, k M + j, L + g, 0). */
+/* loss = sum_frames sum_n w_n sum_l |sum_g B_n[l][g] d_g(n) - phi_l(n)|^2,    */
+/* energy = sum_frames sum_n w_n sum_l |phi_l(n)|^2 (w_n = 1 or 2).           */
+/* B is [M][M][L][G] over (j, k) as oracle_group_B gives it.                  */
+/* ------------------------------------------------------------------------- */
+int oracle_filter_frames_loss(int M, double T, int L, const double *h, const double *c, const double *gamma,
+                              int G, const double *ax, const double *ay, const cplx *B, double r0, double L0,
+                              double noise_level, uint32_t k0, uint32_t k1, uint32_t frame0, uint32_t nwrap,
+                              int nframes, double *loss, double *energy)
+{
+    if (M <= 0 || M % 2 || L <= 0 || G <= 0 || nwrap == 0) return -1;
+    const double omega = PI / T;
+    const int Mh = M / 2;
+    double *var = (double *)malloc(sizeof(double) * (size_t)M * Mh * L);
+    double Ef = 0;
+    for (int k = 0; k < Mh; ++k)
+        for (int j = 0; j < M; ++j)
+            for (int l = 0; l < L; ++l) {
+                double v = 0;
+                if (j != M / 2 && !(j == 0 && k == 0)) {
+                    double nx = shifted_index(j, M), ny = k, per = 2.0 * c[l] * T;
+                    double f2 = (nx * nx + ny * ny) / (per * per);
+                    double r0l = r0 * pow(gamma[l], -3.0 / 5.0);
+                    double psd = 0.023 * pow(r0l, -5.0 / 3.0) * pow(f2 + 1.0 / (L0 * L0), -11.0 / 6.0);
+                    v = pow((double)M, 4) * 0.5 * psd / (per * per);
+                }
+                var[((size_t)k * M + j) * L + l] = v;
+                Ef += (k == 0 ? 1.0 : 2.0) * v;
+            }
+    const double nsd = sqrt(noise_level * noise_level * Ef / ((double)M * M) / 2.0);
+    double *fl = (double *)calloc((size_t)(nframes > 0 ? nframes : 1), sizeof(double));
+    double *fe = (double *)calloc((size_t)(nframes > 0 ? nframes : 1), sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int fr = 0; fr < nframes; ++fr) {
+        double tl = 0, te = 0;
+        uint32_t F = (uint32_t)((frame0 + (uint32_t)fr) % nwrap);
+        double *pr = (double *)malloc(sizeof(double) * 2 * L);
+        cplx *d = (cplx *)malloc(sizeof(cplx) * G);
+        for (int k = 0; k < Mh; ++k)
+            for (int j = 0; j < M; ++j) {
+                if (j == M / 2) continue;
+                uint32_t fi = (uint32_t)(k * M + j);
+                double nx = shifted_index(j, M), ny = k, wn = k == 0 ? 1.0 : 2.0;
+                for (int g = 0; g < G; ++g) d[g] = 0;
+                for (int l = 0; l < L; ++l) {
+                    double z0, z1, sd = sqrt(0.5 * var[(size_t)fi * L + l]);
+                    normal_pair(F, fi, (uint32_t)l, k0, k1, &z0, &z1);
+                    pr[2 * l] = sd * z0;
+                    pr[2 * l + 1] = sd * z1;
+                    for (int g = 0; g < G; ++g) {
+                        double arg = omega * (nx * ax[g] * h[l] + ny * ay[g] * h[l]) / c[l];
+                        d[g] += (cos(arg) + I * sin(arg)) * (pr[2 * l] + I * pr[2 * l + 1]);
+                    }
+                }
+                for (int g = 0; g < G; ++g) {
+                    double z0, z1;
+                    normal_pair(F, fi, (uint32_t)(L + g), k0, k1, &z0, &z1);
+                    d[g] += nsd * (z0 + I * z1);
+                }
+                const cplx *Bf = B + ((size_t)j * M + k) * L * G;
+                for (int l = 0; l < L; ++l) {
+                    cplx rec = 0;
+                    for (int g = 0; g < G; ++g) rec += Bf[l * G + g] * d[g];
+                    cplx e = rec - (pr[2 * l] + I * pr[2 * l + 1]);
+                    tl += wn * (creal(e) * creal(e) + cimag(e) * cimag(e));
+                    te += wn * (pr[2 * l] * pr[2 * l] + pr[2 * l + 1] * pr[2 * l + 1]);
+                }
+            }
+        free(pr);
+        free(d);
+        fl[fr] = tl;
+        fe[fr] = te;
+    }
+    double tl = 0, te = 0;
+    for (int fr = 0; fr < nframes; ++fr) { /* in frame order */
+        tl += fl[fr];
+        te += fe[fr];
+    }
+    free(var);
+    free(fl);
+    free(fe);
+    *loss = tl;
+    *energy = te;
     return 0;
 }

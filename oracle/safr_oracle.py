@@ -23,6 +23,7 @@ _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _cp = np.ctypeslib.ndpointer(dtype=np.complex128, flags="C_CONTIGUOUS")
 _ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _bp = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_up = np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS")
 
 
 def build(force: bool = False) -> str:
@@ -64,6 +65,15 @@ def _load():
                                           C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p]
         lib.oracle_plan_reconstruct.argtypes = [C.c_void_p, _dp, _dp, C.POINTER(C.c_double)]
         lib.oracle_plan_reconstruct_samples.argtypes = [C.c_void_p, _dp, C.c_int, _ip, _dp]
+        lib.oracle_mlp_phi.argtypes = [_dp, _dp]
+        lib.oracle_mlp_phi.restype = C.c_double
+        lib.oracle_group_B_learned.argtypes = [C.c_int, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp,
+                                               C.c_double, _dp, C.c_double, _cp]
+        lib.oracle_philox4x32_10.argtypes = [_up, _up, _up]
+        lib.oracle_filter_frames_loss.argtypes = [C.c_int, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp,
+                                                  _cp, C.c_double, C.c_double, C.c_double, C.c_uint32,
+                                                  C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
+                                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = lib
         return lib
 
@@ -126,6 +136,50 @@ def group_B(M, T, h, c, gamma, ax, ay, alpha, beta) -> np.ndarray:
     if rc:
         raise ValueError("oracle_group_B: bad arguments")
     return B
+
+
+MLP_PARAMS = 4 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1
+
+
+def mlp_phi(params: np.ndarray, x) -> float:
+    """Filter factor phi in (0, 1) of the learned filter's MLP at features x[4]."""
+    return _load().oracle_mlp_phi(_f64(params), _f64(x))
+
+
+def group_B_learned(M, T, h, c, gamma, ax, ay, beta, params, noise_level) -> np.ndarray:
+    """Section 3.1's filtered inverse with the learned filter phi / sigma: B [M][M][L][G]."""
+    h, c, gamma, ax, ay, params = map(_f64, (h, c, gamma, ax, ay, params))
+    if params.size != MLP_PARAMS:
+        raise ValueError("wrong parameter count")
+    L, G = len(h), len(ax)
+    B = np.empty((M, M, L, G), np.complex128)
+    if _load().oracle_group_B_learned(M, float(T), L, h, c, gamma, G, ax, ay, float(beta), params,
+                                      float(noise_level), B):
+        raise ValueError("oracle_group_B_learned: bad arguments")
+    return B
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block (Salmon et al., SC 2011): 4 output words."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.empty(4, np.uint32)
+    _load().oracle_philox4x32_10(c, k, out)
+    return out
+
+
+def filter_frames_loss(M, T, h, c, gamma, ax, ay, B, r0, L0, noise_level, key, frame0, nwrap, nframes):
+    """(loss, energy) of reconstruction B [M][M][L][G] on the learned filter's
+    Fourier-domain training frames (layered model of Section 2)."""
+    h, c, gamma, ax, ay = map(_f64, (h, c, gamma, ax, ay))
+    B = _c128(B)
+    L, G = len(h), len(ax)
+    loss, energy = C.c_double(), C.c_double()
+    if _load().oracle_filter_frames_loss(M, float(T), L, h, c, gamma, G, ax, ay, B, float(r0), float(L0),
+                                         float(noise_level), int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF,
+                                         int(frame0), int(nwrap), int(nframes), C.byref(loss), C.byref(energy)):
+        raise ValueError("oracle_filter_frames_loss: bad arguments")
+    return loss.value, energy.value
 
 
 def pupil_mask(P: int, delta: float, D: float, obstruction: float) -> np.ndarray:

@@ -50,6 +50,7 @@ void free_plan_memory(safr_plan_s *p)
         if (b) cudaFree(b);
     for (auto &e : p->ev)
         if (e) cudaEventDestroy(e);
+    safr::filter_free(p);
 }
 
 // Inverse of a 3x3 matrix by cofactors; false if singular.

@@ -130,6 +130,10 @@ struct safr_plan_s {
     float *d_in_scales_stage = nullptr, *d_out_scales_stage = nullptr;
     size_t in_bytes = 0, out_bytes = 0;
 
+    // learned spectral filter (learned.cu): device state, allocated on first use
+    void *filter = nullptr;
+    int filter_learned = 0;  // 1: B holds the learned filter's inverse
+
     // tracing
     int trace = 0;
     int traced = 0;
@@ -147,6 +151,7 @@ bool configure_fused(safr_plan_s *plan);
 cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scales, void *out, float *out_scales,
                          cudaStream_t stream);
 void frame2_twiddles(int M, std::vector<double> &re, std::vector<double> &im);
+void filter_free(safr_plan_s *plan);
 inline bool use_fused(const safr_plan_s *plan)
 {
     return plan->fused_ok && plan->path != SAFR_PATH_PASSES;

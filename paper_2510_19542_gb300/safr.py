@@ -37,8 +37,10 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_launches_per_frame", "safr_trace_phases", "safr_set_path", "safr_get_path", "safr_debug_skip_barrier",
             "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc", "safr_autotune",
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
-            "safr_batch_destroy", "safr_batch_graph"]
+            "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
+            "safr_filter_reset"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
+SAFR_FILTER_PARAMS = 8705
 
 
 class SafrError(RuntimeError):
@@ -62,6 +64,17 @@ class safr_plan_info(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("in_bytes", C.c_size_t), ("out_bytes", C.c_size_t),
                 ("warnings", C.c_int), ("precomputed", C.c_int), ("path", C.c_int), ("tile_rows", C.c_int),
                 ("autotuned", C.c_int)]
+
+
+class safr_filter_config(C.Structure):
+    _fields_ = [("r0", C.c_double), ("L0", C.c_double), ("noise_level", C.c_double), ("train_frames", C.c_int),
+                ("valid_frames", C.c_int), ("epochs", C.c_int), ("lr", C.c_double), ("seed", C.c_ulonglong)]
+
+
+class safr_filter_result(C.Structure):
+    _fields_ = [("train_loss_first", C.c_double), ("train_loss_last", C.c_double),
+                ("valid_loss_learned", C.c_double), ("valid_loss_plain", C.c_double), ("steps", C.c_long),
+                ("used_learned", C.c_int), ("nonfinite", C.c_int), ("noise_sd", C.c_double)]
 
 
 _lib = None
@@ -106,6 +119,10 @@ def load(build_if_missing: bool = True):
     lib.safr_batch_launches.argtypes = [vp]
     lib.safr_batch_graph.argtypes = [vp]
     lib.safr_batch_destroy.argtypes = [vp]
+    lib.safr_filter_train.argtypes = [vp, C.POINTER(safr_filter_config), C.POINTER(C.c_float),
+                                      C.POINTER(safr_filter_result), vp]
+    lib.safr_filter_apply.argtypes = [vp, C.POINTER(C.c_float), C.c_double, vp]
+    lib.safr_filter_reset.argtypes = [vp, vp]
     lib.safr_status_string.argtypes = [C.c_int]
     lib.safr_status_string.restype = C.c_char_p
     for name in _EXPORTS:
@@ -267,6 +284,32 @@ def safr_reconstruct_noalloc(cuda_device: int, M: int, P: int, L: int, G: int, B
 
 def safr_autotune(plan: int, stream=None):
     _check(load().safr_autotune(plan, _stream(stream)), "safr_autotune")
+
+
+def safr_filter_train(plan: int, r0: float, L0: float, noise_level: float, train_frames: int, valid_frames: int,
+                      epochs: int, lr: float = 2e-3, seed: int = 5, stream=None):
+    """Train the learned spectral filter on the GPU; returns (weights [SAFR_FILTER_PARAMS]
+    float32, rounded to BF16, and the result fields as a dict)."""
+    cfg = safr_filter_config(float(r0), float(L0), float(noise_level), int(train_frames), int(valid_frames),
+                             int(epochs), float(lr), int(seed))
+    w = np.zeros(SAFR_FILTER_PARAMS, np.float32)
+    res = safr_filter_result()
+    _check(load().safr_filter_train(plan, C.byref(cfg), w.ctypes.data_as(C.POINTER(C.c_float)), C.byref(res),
+                                    _stream(stream)), "safr_filter_train")
+    return w, {name: getattr(res, name) for name, _ in safr_filter_result._fields_}
+
+
+def safr_filter_apply(plan: int, weights, noise_level: float, stream=None):
+    """B from the given MLP parameters (host float32 array of SAFR_FILTER_PARAMS)."""
+    w = np.ascontiguousarray(weights, np.float32)
+    if w.size != SAFR_FILTER_PARAMS:
+        raise ValueError(f"expected {SAFR_FILTER_PARAMS} parameters, got {w.size}")
+    _check(load().safr_filter_apply(plan, w.ctypes.data_as(C.POINTER(C.c_float)), float(noise_level),
+                                    _stream(stream)), "safr_filter_apply")
+
+
+def safr_filter_reset(plan: int, stream=None):
+    _check(load().safr_filter_reset(plan, _stream(stream)), "safr_filter_reset")
 
 
 def _ptr_array(xs):

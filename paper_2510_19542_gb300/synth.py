@@ -48,6 +48,9 @@ def config(k: int) -> dict:
        9 layers 0-16 km with an exponential Cn2 profile, r0 0.157 m, 2% noise, FP32.
     3: 8 m pupil filling a 512x512 grid, 3 NGS at 1 arcmin, 35 layers 0-20 km,
        exponential Cn2, r0 0.15 m, 1% noise, FP16 storage with per-layer scales.
+    5: the geometry of 1 (8 m, 32x32 grid, 3 NGS at 1 arcmin) with 35 layers
+       0-20 km on the exponential Cn2 profile, r0 0.15 m, 1% noise, FP32: the
+       learned spectral filter's workload.
     """
     if k == 1:
         ax, ay = _ring(1.0, [0.0, 120.0, 240.0])
@@ -75,6 +78,9 @@ def config(k: int) -> dict:
                     kind=np.zeros(3, np.int32), h_lgs=90e3, alpha=0.005, alpha_tt=0.01, beta=1.5,
                     output_metric=1, remove_tt=1, precision="fp16", r0=0.15, L0=25.0,
                     noise=0.01, seed=3)
+    if k == 5:
+        h = np.linspace(0.0, 20000.0, 35)
+        return dict(config(1), name="learned-ngs-32-L35", h=h, cn2=_exp_profile(h), precision="fp32", seed=5)
     raise ValueError(f"no workload {k}")
 
 
@@ -161,6 +167,17 @@ def frame(geom: dict, seed: int | None = None, noise: float | None = None,
     if return_truth:
         return out, coeffs
     return out
+
+
+def truth_layers(geom: dict, coeffs) -> np.ndarray:
+    """The screens of frame(..., return_truth=True) on the M x M grid x_p =
+    -T + p * pitch (layer pitch = pupil pitch: NGS geometry), [L][M][M]."""
+    M, d = geom["M"], geom["pitch"]
+    T = M * d / 2.0
+    x = -T + np.arange(M) * d
+    n = np.arange(-(M // 2 - 1), M // 2)
+    e = np.exp(1j * (math.pi / T) * np.outer(x, n))
+    return np.stack([(e @ c @ e.T).real for c in coeffs])
 
 
 def random_frame(geom: dict, seed: int) -> np.ndarray:

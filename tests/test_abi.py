@@ -82,6 +82,19 @@ def test_null_arguments(lib):
     assert lib.safr_reconstruct(None, None, None, None, None, None) == safr.SAFR_ERR_INVALID_ARG
     assert lib.safr_destroy(None) == safr.SAFR_ERR_INVALID_ARG
     assert lib.safr_launches_per_frame(None) == 0
+    assert lib.safr_filter_train(None, None, None, None, None) == safr.SAFR_ERR_INVALID_ARG
+    cfg = safr.safr_filter_config(0.15, 25.0, 0.01, 1000, 256, 1, 2e-3, 5)
+    assert lib.safr_filter_train(None, C.byref(cfg), None, None, None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_filter_apply(None, None, 0.01, None) == safr.SAFR_ERR_INVALID_ARG
+    assert lib.safr_filter_reset(None, None) == safr.SAFR_ERR_INVALID_ARG
+
+
+def test_filter_parameter_count_matches_the_header():
+    """SAFR_FILTER_PARAMS = 4*64 + 64 + 2*(64*64 + 64) + 64 + 1 (MLP 4-64-64-64-1)."""
+    from paper_2510_19542_gb300 import safr
+    src = open(os.path.join(ROOT, "include", "safr.h")).read()
+    declared = int(re.search(r"#define SAFR_FILTER_PARAMS (\d+)", src).group(1))
+    assert declared == safr.SAFR_FILTER_PARAMS == 4 * 64 + 64 + 2 * (64 * 64 + 64) + 64 + 1
 
 
 def test_plan_create_without_gpu_reports_cuda_error(lib):
