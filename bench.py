@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "passes"])
-    ap.add_argument("--no-workloads", action="store_true", help="skip the 32-grid and 512-grid workloads")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the 32-grid, 512-grid, batched and learned-filter workloads")
     return ap.parse_args()
 
 
@@ -311,6 +311,92 @@ def measure_batch(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm,
     return "batched-64-uneven", out
 
 
+def measure_learned(safr, synth, torch, dev, stream, steps, warmup, flush_l2):
+    """The learned spectral filter on the 32-grid geometry with 35 layers: GPU
+    training on 100k forward-model frames (2 epochs), the held-out comparison
+    with plain SAFR, the time to rebuild B from the weights, frames with the
+    learned B (the same frame kernel), the learned B against the FP64 oracle,
+    and the layer error against the true screens of 8 synthetic frames for both
+    filters."""
+    import time
+
+    import oracle
+    g = synth.config(5)
+    plan = safr.Plan(g, device=dev.index)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    w, res = safr.safr_filter_train(plan.handle, g["r0"], g["L0"], g["noise"], 100000, 4096, 2, lr=1e-3, seed=5,
+                                    stream=stream)
+    torch.cuda.synchronize(dev)
+    train_s = time.perf_counter() - t0
+    used = res["used_learned"]
+    ta = []
+    for _ in range(5):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        safr.safr_filter_apply(plan.handle, w, g["noise"], stream=stream)
+        ta.append((time.perf_counter() - t0) * 1e3)
+    # the learned B against the oracle's, from the same BF16 parameters
+    M = g["M"]
+    cn2 = np.asarray(g["cn2"], np.float64)
+    Bo = oracle.group_B_learned(M, M * g["pitch"] / 2.0, np.asarray(g["h"], np.float64), np.ones(len(g["h"])),
+                                cn2 / cn2.sum(), np.asarray(g["dir_x"], np.float64),
+                                np.asarray(g["dir_y"], np.float64), g["beta"], w.astype(np.float64), g["noise"])
+    Bo = np.transpose(Bo[:, :M // 2], (1, 2, 3, 0))
+    Bg = safr.safr_copy_B(plan.handle, 0)
+    b_err = float(np.abs(Bg - Bo).max() / np.abs(Bo).max())
+    # frames with the learned B
+    xin = torch.from_numpy(synth.frame(g, seed=600).astype(np.float32)).to(dev)
+    layers = plan.empty_layers()
+
+    def one(i):
+        flush_l2(i)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        safr.safr_reconstruct(plan.handle, xin, layers, stream=stream)
+        e.record(stream)
+        e.synchronize()
+        return a.elapsed_time(e)
+
+    for i in range(warmup):
+        one(i)
+    lat = sorted(one(i) for i in range(steps))
+
+    def truth_error():
+        num = den = 0.0
+        for sd in range(500, 508):
+            x, coeffs = synth.frame(g, seed=sd, return_truth=True)
+            out = plan.reconstruct(torch.from_numpy(x.astype(np.float32)).to(dev), stream=stream)
+            torch.cuda.synchronize(dev)
+            t = synth.truth_layers(g, coeffs)
+            num += float(np.sum((out.double().cpu().numpy() - t) ** 2))
+            den += float(np.sum(t ** 2))
+        return num / den
+
+    e_learned = truth_error()
+    safr.safr_filter_reset(plan.handle, stream=stream)
+    e_plain = truth_error()
+    if not used:  # the plan kept plain SAFR
+        e_learned = e_plain
+    mean_ms = float(np.mean(lat))
+    out = {"grid": M, "stars": len(g["dir_x"]), "layers": len(g["h"]), "precision": "fp32 (MLP: bf16 weights)",
+           "train": {"frames": 100000, "epochs": 2, "steps": res["steps"], "s": train_s,
+                     "frames_per_s": res["steps"] * 256 / train_s,
+                     "loss_first": res["train_loss_first"], "loss_last": res["train_loss_last"]},
+           "heldout_rel_sq_error": {"learned": res["valid_loss_learned"], "plain_safr": res["valid_loss_plain"],
+                                    "frames": 4096},
+           "used_learned": used, "nonfinite": res["nonfinite"],
+           "rebuild_B_ms": float(np.median(ta)), "B_max_rel_err_vs_oracle": b_err,
+           "synthetic_frames_rel_sq_error_vs_truth": {"learned": e_learned, "plain_safr": e_plain, "frames": 8},
+           "frames_per_s": 1e3 / mean_ms,
+           "latency_ms": {"p50": lat[len(lat) // 2],
+                          "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+           "steps": steps}
+    plan.close()
+    return g["name"], out
+
+
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
@@ -445,6 +531,8 @@ def run_safr(args):
                                          hbm_pk)
             workloads[name] = res
         name, res = measure_batch(safr, synth, torch, dev, stream, min(args.steps, 20), 3, flush_l2, hbm_pk)
+        workloads[name] = res
+        name, res = measure_learned(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2)
         workloads[name] = res
 
     if rank == 0:
