@@ -93,7 +93,7 @@ typedef struct {
     int M;                 /* periodic grid size: power of two, 8 <= M <= 1024            */
     int P;                 /* pupil samples across, 1 <= P <= M                           */
     double pitch_m;        /* grid pitch delta = 2T/M in metres (T = M delta / 2)          */
-    double diameter_m;     /* pupil diameter D (annulus mask, removeTT only); <= 0: square */
+    double diameter_m;     /* pupil diameter D (annulus mask: removeTT, learned-filter training); <= 0: square */
     double obstruction;    /* central obstruction as a fraction of D                      */
     int L;                 /* number of layers, 1 <= L <= SAFR_MAX_L                      */
     const double *h_m;     /* [L] layer heights, ascending, 0 <= h_l < h_lgs_m             */
@@ -387,23 +387,30 @@ typedef struct {
     long steps;                /* Adam steps (256 frames each) */
     int used_learned;          /* 1: B now holds the learned filter's inverse */
     int nonfinite;             /* 1: the MLP gave a non-finite weight */
-    double noise_sd;           /* std of the real and imaginary parts of the spectral noise */
 } safr_filter_result;
 
 /*
- * safr_filter_train: trains the MLP on the GPU.  Training frames come from
- * the SAFR forward model in the Fourier domain, d_g(n) = sum_l
- * exp(i theta_gl(n)) phi_l(n) + eta_g(n), with layer spectra phi_l of von
- * Karman screens (cfg r0, L0, the plan's Cn2 weights and layer periods) and
- * white noise eta of cfg->noise_level, drawn from Philox4x32-10 (Salmon et
- * al., SC 2011).  Frame F takes phi_l(n), n = (j, k) with k < M/2, from the
- * Box-Muller pair of counter (F, k M + j, l, 0) and eta_g(n) from
- * (F, k M + j, L + g, 0); the training frames use key (seed mod 2^32,
- * (seed >> 32) xor 0x5AFE), the held-out frames key (seed mod 2^32 + 1,
+ * safr_filter_train: trains the MLP on the GPU.  Training frames follow the
+ * layered model of Section 2 through the aperture: layer spectra phi_l of
+ * von Karman screens (cfg r0, L0, the plan's Cn2 weights and layer periods),
+ * the noise-free data spectrum c_g(n) = sum_l exp(i theta_gl(n)) phi_l(n),
+ * the wavefront psi_g = IDFT2(c_g) restricted to the plan's pupil (the P x P
+ * square at offset (M - P)/2, masked by the annulus when a diameter is
+ * given), plus white noise on the pupil pixels with a std of
+ * cfg->noise_level x the RMS of the masked noise-free wavefront (per frame
+ * and star), and d_g = DFT2 of that.  Random numbers come from
+ * Philox4x32-10 (Salmon et al., SC 2011) and Box-Muller: frame F takes
+ * phi_l(n), n = (j, k) with k < M/2, from counter (F, k M + j, l, 0), the
+ * row k = 0 holding conjugate pairs (j > M/2 is the conjugate of M - j), and
+ * the noise at grid pixel (p, q) of star g from the first normal of counter
+ * (F, p M + q, g, 1).  Training frames use key (seed mod 2^32,
+ * (seed >> 32) xor 0x5AFE), held-out frames key (seed mod 2^32 + 1,
  * (seed >> 32) xor 0x5AFE).  E|phi_l(n)|^2 = M^4 PSD_l(|n| / (2 c_l T)) /
- * (2 (2 c_l T)^2) (half the power per complex coefficient of a real screen)
- * and E|eta_g(n)|^2 = noise^2 E_f / M^2, E_f the expected spectral energy of
- * one frame (a per-pixel noise std of noise x the data's RMS).  The loss is the relative squared error of the reconstructed
+ * (2 (2 c_l T)^2), half the power per complex coefficient of a real screen.
+ * Training needs M <= 64 (SAFR_ERR_UNSUPPORTED_SIZE otherwise).  Frames are
+ * processed 256 at a time, so held-out frames are taken in multiples of 256
+ * (indices wrap modulo valid_frames).  The loss is
+ * the relative squared error of the reconstructed
  * layer spectra, minimised by Adam (FP32 master weights, BF16 copy used by
  * the MLP) over ceil(train_frames / 256) * epochs steps of 256 frames.
  * Held-out frames (another key) then compare the learned filter with plain

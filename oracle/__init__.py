@@ -18,6 +18,7 @@ from .safr_oracle import (  # noqa: F401
     mlp_phi,
     philox4x32_10,
     filter_frames_loss,
+    filter_frame,
     MLP_PARAMS,
     cone,
     remove_tt,

@@ -661,10 +661,11 @@ void oracle_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *ou
 }
 
 /* Two standard normals by Box-Muller from the first two output words of    */
-/* counter (a, b, c, 0): u = (word + 1/2) 2^-32 in (0, 1).                  */
-static void normal_pair(uint32_t a, uint32_t b, uint32_t c, uint32_t k0, uint32_t k1, double *z0, double *z1)
+/* counter (a, b, c, e): u = (word + 1/2) 2^-32 in (0, 1).                  */
+static void normal_pair(uint32_t a, uint32_t b, uint32_t c, uint32_t e, uint32_t k0, uint32_t k1, double *z0,
+                        double *z1)
 {
-    uint32_t ctr[4] = {a, b, c, 0u}, key[2] = {k0, k1}, o[4];
+    uint32_t ctr[4] = {a, b, c, e}, key[2] = {k0, k1}, o[4];
     oracle_philox4x32_10(ctr, key, o);
     double u1 = ((double)o[0] + 0.5) / 4294967296.0, u2 = ((double)o[1] + 0.5) / 4294967296.0;
     double rad = sqrt(-2.0 * log(u1));
@@ -673,34 +674,44 @@ static void normal_pair(uint32_t a, uint32_t b, uint32_t c, uint32_t k0, uint32_
 }
 
 /* ------------------------------------------------------------------------- */
-/* Training frames of the learned filter and the error of a reconstruction  */
-/* B on them.  Frames follow the layered model of Section 2 in the Fourier   */
-/* domain: the data of star g at frequency n is                              */
-/*   d_g(n) = sum_l exp(i omega n.(alpha_g h_l) / c_l) phi_l(n) + eta_g(n),   */
-/* phi_l(n) the DFT of layer l over its own M x M grid (pitch c_l delta,     */
-/* period 2 c_l T), complex normal with E|phi_l(n)|^2 =                       */
-/*   M^4 (1/2) PSD_l(|n| / (2 c_l T)) / (2 c_l T)^2,                          */
-/*   PSD_l(f) = 0.023 (r0 gamma_l^{-3/5})^{-5/3} (f^2 + L0^-2)^{-11/6}         */
-/* (von Karman; zero at n = 0), and eta_g white with E|eta|^2 =               */
-/* noise^2 E_f / M^2, E_f = sum over the full spectrum of sum_l E|phi_l|^2     */
-/* (a per-pixel noise std of noise x the data's RMS).  Frequencies k in       */
-/* [0, M/2), j in [0, M) with j != M/2 are drawn; the others follow from      */
-/* conjugate symmetry and count twice for k > 0.  Frame F draws phi_l(n) from */
-/* Philox counter (F, k M + j, l, 0) and eta_g(n) from (F, k M + j, L + g, 0). */
-/* loss = sum_frames sum_n w_n sum_l |sum_g B_n[l][g] d_g(n) - phi_l(n)|^2,    */
-/* energy = sum_frames sum_n w_n sum_l |phi_l(n)|^2 (w_n = 1 or 2).           */
-/* B is [M][M][L][G] over (j, k) as oracle_group_B gives it.                  */
+/* Training frames of the learned filter: the layered model of Section 2     */
+/* seen through the aperture.                                                 */
+/*   phi_l(n): the DFT of layer l over its own M x M grid (pitch c_l delta,   */
+/*     period 2 c_l T), complex normal with E|phi_l(n)|^2 =                   */
+/*     M^4 (1/2) PSD_l(|n| / (2 c_l T)) / (2 c_l T)^2,                        */
+/*     PSD_l(f) = 0.023 (r0 gamma_l^{-3/5})^{-5/3} (f^2 + L0^-2)^{-11/6}       */
+/*     (von Karman; half the power per complex coefficient of a real screen; */
+/*     zero at n = 0 and on the Nyquist row and column);                     */
+/*   phi_l(-n) = conj(phi_l(n)), so each layer is real;                      */
+/*   c_g(n) = sum_l exp(i omega n.(alpha_g h_l) / c_l) phi_l(n);               */
+/*   psi_g = IDFT2(c_g) on the pupil (P x P at offset (M-P)/2, annulus mask   */
+/*     of diameter D when D > 0), zero elsewhere, plus white noise of std     */
+/*     noise x RMS of the masked noise-free psi_g on the pupil pixels;        */
+/*   d_g = DFT2(psi_g).                                                      */
+/* Random numbers: Philox4x32-10 and Box-Muller.  Frame F draws phi_l(j, k),  */
+/* k < M/2, from counter (F, k M + j, l, 0), the row k = 0 taking j > M/2 as  */
+/* the conjugate of M - j, and the noise at grid pixel (p, q) of star g from  */
+/* the first normal of counter (F, p M + q, g, 1).                            */
 /* ------------------------------------------------------------------------- */
-int oracle_filter_frames_loss(int M, double T, int L, const double *h, const double *c, const double *gamma,
-                              int G, const double *ax, const double *ay, const cplx *B, double r0, double L0,
-                              double noise_level, uint32_t k0, uint32_t k1, uint32_t frame0, uint32_t nwrap,
-                              int nframes, double *loss, double *energy)
+typedef struct {
+    int M, L, G, P;
+    double T, D, obstruction, noise;
+    const double *h, *c, *ax, *ay;
+    uint32_t k0, k1;
+    double *var;          /* [M/2][M][L] */
+    unsigned char *mask;  /* [M][M] */
+} frame_model;
+
+static int frame_model_init(frame_model *fm, int M, double T, int L, const double *h, const double *c,
+                            const double *gamma, int G, const double *ax, const double *ay, int P, double D,
+                            double obstruction, double r0, double L0, double noise, uint32_t k0, uint32_t k1)
 {
-    if (M <= 0 || M % 2 || L <= 0 || G <= 0 || nwrap == 0) return -1;
-    const double omega = PI / T;
+    if (M <= 0 || M % 2 || L <= 0 || G <= 0 || P <= 0 || P > M) return -1;
     const int Mh = M / 2;
-    double *var = (double *)malloc(sizeof(double) * (size_t)M * Mh * L);
-    double Ef = 0;
+    fm->M = M; fm->L = L; fm->G = G; fm->P = P; fm->T = T; fm->D = D; fm->obstruction = obstruction;
+    fm->noise = noise; fm->h = h; fm->c = c; fm->ax = ax; fm->ay = ay; fm->k0 = k0; fm->k1 = k1;
+    fm->var = (double *)malloc(sizeof(double) * (size_t)Mh * M * L);
+    fm->mask = (unsigned char *)calloc((size_t)M * M, 1);
     for (int k = 0; k < Mh; ++k)
         for (int j = 0; j < M; ++j)
             for (int l = 0; l < L; ++l) {
@@ -712,59 +723,145 @@ int oracle_filter_frames_loss(int M, double T, int L, const double *h, const dou
                     double psd = 0.023 * pow(r0l, -5.0 / 3.0) * pow(f2 + 1.0 / (L0 * L0), -11.0 / 6.0);
                     v = pow((double)M, 4) * 0.5 * psd / (per * per);
                 }
-                var[((size_t)k * M + j) * L + l] = v;
-                Ef += (k == 0 ? 1.0 : 2.0) * v;
+                fm->var[((size_t)k * M + j) * L + l] = v;
             }
-    const double nsd = sqrt(noise_level * noise_level * Ef / ((double)M * M) / 2.0);
+    unsigned char *pm = (unsigned char *)malloc((size_t)P * P);
+    if (D > 0) oracle_pupil_mask(P, 2.0 * T / M, D, obstruction, pm);
+    else memset(pm, 1, (size_t)P * P);
+    const int o = (M - P) / 2;
+    for (int a = 0; a < P; ++a)
+        for (int b = 0; b < P; ++b) fm->mask[(size_t)(o + a) * M + o + b] = pm[(size_t)a * P + b];
+    free(pm);
+    return 0;
+}
+
+static void frame_model_free(frame_model *fm)
+{
+    free(fm->var);
+    free(fm->mask);
+}
+
+/* phi [M/2][M][L] (stored half, k < M/2) and d [G][M][M] of frame F. */
+static void frame_draw(const frame_model *fm, uint32_t F, cplx *phi, cplx *d)
+{
+    const int M = fm->M, Mh = M / 2, L = fm->L, G = fm->G;
+    const double omega = PI / fm->T;
+    for (int k = 0; k < Mh; ++k)
+        for (int j = 0; j < M; ++j)
+            for (int l = 0; l < L; ++l) {
+                int flip = k == 0 && j > M / 2;
+                int jj = flip ? M - j : j;
+                double z0, z1, sd = sqrt(0.5 * fm->var[((size_t)k * M + jj) * L + l]);
+                normal_pair(F, (uint32_t)(k * M + jj), (uint32_t)l, 0u, fm->k0, fm->k1, &z0, &z1);
+                phi[((size_t)k * M + j) * L + l] = sd * z0 + I * (flip ? -sd * z1 : sd * z1);
+            }
+    cplx *cs = (cplx *)malloc(sizeof(cplx) * (size_t)M * M);
+    cplx *ps = (cplx *)malloc(sizeof(cplx) * (size_t)M * M);
+    for (int g = 0; g < G; ++g) {
+        for (int j = 0; j < M; ++j)
+            for (int k = 0; k < M; ++k) {
+                cplx v = 0;
+                if (j != M / 2 && k != M / 2) {
+                    /* phi at n or, for k > M/2, the conjugate of phi at -n */
+                    int neg = k > M / 2;
+                    int js = neg ? (M - j) % M : j, ks = neg ? M - k : k;
+                    double nx = shifted_index(j, M), ny = shifted_index(k, M);
+                    for (int l = 0; l < L; ++l) {
+                        cplx p = phi[((size_t)ks * M + js) * L + l];
+                        if (neg) p = conj(p);
+                        double arg = omega * (nx * fm->ax[g] * fm->h[l] + ny * fm->ay[g] * fm->h[l]) / fm->c[l];
+                        v += (cos(arg) + I * sin(arg)) * p;
+                    }
+                }
+                cs[(size_t)j * M + k] = v;
+            }
+        oracle_dft2(M, cs, ps, 1);
+        double s2 = 0;
+        int cnt = 0;
+        for (int i = 0; i < M * M; ++i) {
+            double v = fm->mask[i] ? creal(ps[i]) : 0.0;
+            ps[i] = v;
+            if (fm->mask[i]) {
+                s2 += v * v;
+                ++cnt;
+            }
+        }
+        double sigma = cnt ? fm->noise * sqrt(s2 / cnt) : 0.0;
+        if (sigma > 0)
+            for (int i = 0; i < M * M; ++i)
+                if (fm->mask[i]) {
+                    double z0, z1;
+                    normal_pair(F, (uint32_t)i, (uint32_t)g, 1u, fm->k0, fm->k1, &z0, &z1);
+                    ps[i] += sigma * z0;
+                }
+        oracle_dft2(M, ps, d + (size_t)g * M * M, 0);
+    }
+    free(cs);
+    free(ps);
+}
+
+int oracle_filter_frame(int M, double T, int L, const double *h, const double *c, const double *gamma, int G,
+                        const double *ax, const double *ay, int P, double D, double obstruction, double r0,
+                        double L0, double noise_level, uint32_t k0, uint32_t k1, uint32_t F, cplx *phi, cplx *d)
+{
+    frame_model fm;
+    if (frame_model_init(&fm, M, T, L, h, c, gamma, G, ax, ay, P, D, obstruction, r0, L0, noise_level, k0, k1))
+        return -1;
+    frame_draw(&fm, F, phi, d);
+    frame_model_free(&fm);
+    return 0;
+}
+
+/* loss = sum_frames sum_n w_n sum_l |sum_g B_n[l][g] d_g(n) - phi_l(n)|^2 and       */
+/* energy = sum_frames sum_n w_n sum_l |phi_l(n)|^2 over the stored frequencies      */
+/* (k < M/2, j != M/2; w_n = 1 on the row k = 0, which holds both n and -n, else 2). */
+/* B is [M][M][L][G] over (j, k) as oracle_group_B gives it.  Frames                 */
+/* (frame0 + i) mod nwrap, i < nframes.                                              */
+int oracle_filter_frames_loss(int M, double T, int L, const double *h, const double *c, const double *gamma,
+                              int G, const double *ax, const double *ay, const cplx *B, int P, double D,
+                              double obstruction, double r0, double L0, double noise_level, uint32_t k0,
+                              uint32_t k1, uint32_t frame0, uint32_t nwrap, int nframes, double *loss,
+                              double *energy)
+{
+    if (nwrap == 0 || nframes < 0) return -1;
+    frame_model fm;
+    if (frame_model_init(&fm, M, T, L, h, c, gamma, G, ax, ay, P, D, obstruction, r0, L0, noise_level, k0, k1))
+        return -1;
+    const int Mh = M / 2;
     double *fl = (double *)calloc((size_t)(nframes > 0 ? nframes : 1), sizeof(double));
     double *fe = (double *)calloc((size_t)(nframes > 0 ? nframes : 1), sizeof(double));
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for schedule(dynamic, 1)
     for (int fr = 0; fr < nframes; ++fr) {
-        double tl = 0, te = 0;
         uint32_t F = (uint32_t)((frame0 + (uint32_t)fr) % nwrap);
-        double *pr = (double *)malloc(sizeof(double) * 2 * L);
-        cplx *d = (cplx *)malloc(sizeof(cplx) * G);
+        cplx *phi = (cplx *)malloc(sizeof(cplx) * (size_t)Mh * M * L);
+        cplx *d = (cplx *)malloc(sizeof(cplx) * (size_t)G * M * M);
+        frame_draw(&fm, F, phi, d);
+        double tl = 0, te = 0;
         for (int k = 0; k < Mh; ++k)
             for (int j = 0; j < M; ++j) {
                 if (j == M / 2) continue;
-                uint32_t fi = (uint32_t)(k * M + j);
-                double nx = shifted_index(j, M), ny = k, wn = k == 0 ? 1.0 : 2.0;
-                for (int g = 0; g < G; ++g) d[g] = 0;
-                for (int l = 0; l < L; ++l) {
-                    double z0, z1, sd = sqrt(0.5 * var[(size_t)fi * L + l]);
-                    normal_pair(F, fi, (uint32_t)l, k0, k1, &z0, &z1);
-                    pr[2 * l] = sd * z0;
-                    pr[2 * l + 1] = sd * z1;
-                    for (int g = 0; g < G; ++g) {
-                        double arg = omega * (nx * ax[g] * h[l] + ny * ay[g] * h[l]) / c[l];
-                        d[g] += (cos(arg) + I * sin(arg)) * (pr[2 * l] + I * pr[2 * l + 1]);
-                    }
-                }
-                for (int g = 0; g < G; ++g) {
-                    double z0, z1;
-                    normal_pair(F, fi, (uint32_t)(L + g), k0, k1, &z0, &z1);
-                    d[g] += nsd * (z0 + I * z1);
-                }
+                double wn = k == 0 ? 1.0 : 2.0;
                 const cplx *Bf = B + ((size_t)j * M + k) * L * G;
                 for (int l = 0; l < L; ++l) {
                     cplx rec = 0;
-                    for (int g = 0; g < G; ++g) rec += Bf[l * G + g] * d[g];
-                    cplx e = rec - (pr[2 * l] + I * pr[2 * l + 1]);
+                    for (int g = 0; g < G; ++g) rec += Bf[l * G + g] * d[(size_t)g * M * M + (size_t)j * M + k];
+                    cplx p = phi[((size_t)k * M + j) * L + l];
+                    cplx e = rec - p;
                     tl += wn * (creal(e) * creal(e) + cimag(e) * cimag(e));
-                    te += wn * (pr[2 * l] * pr[2 * l] + pr[2 * l + 1] * pr[2 * l + 1]);
+                    te += wn * (creal(p) * creal(p) + cimag(p) * cimag(p));
                 }
             }
-        free(pr);
-        free(d);
         fl[fr] = tl;
         fe[fr] = te;
+        free(phi);
+        free(d);
     }
     double tl = 0, te = 0;
     for (int fr = 0; fr < nframes; ++fr) { /* in frame order */
         tl += fl[fr];
         te += fe[fr];
     }
-    free(var);
+    frame_model_free(&fm);
     free(fl);
     free(fe);
     *loss = tl;

@@ -71,9 +71,12 @@ def _load():
                                                C.c_double, _dp, C.c_double, _cp]
         lib.oracle_philox4x32_10.argtypes = [_up, _up, _up]
         lib.oracle_filter_frames_loss.argtypes = [C.c_int, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp,
-                                                  _cp, C.c_double, C.c_double, C.c_double, C.c_uint32,
-                                                  C.c_uint32, C.c_uint32, C.c_uint32, C.c_int,
-                                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]
+                                                  _cp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                                  C.c_double, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                                                  C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.oracle_filter_frame.argtypes = [C.c_int, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp,
+                                            C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                            C.c_uint32, C.c_uint32, C.c_uint32, _cp, _cp]
         _lib = lib
         return lib
 
@@ -168,16 +171,33 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return out
 
 
-def filter_frames_loss(M, T, h, c, gamma, ax, ay, B, r0, L0, noise_level, key, frame0, nwrap, nframes):
+def filter_frame(M, T, h, c, gamma, ax, ay, P, D, obstruction, r0, L0, noise_level, key, F):
+    """One training frame of the learned filter (Section 2's layered model through
+    the aperture): layer spectra phi [M/2][M][L] (k < M/2, j, l) and data spectra
+    d [G][M][M] (j, k)."""
+    h, c, gamma, ax, ay = map(_f64, (h, c, gamma, ax, ay))
+    L, G = len(h), len(ax)
+    phi = np.empty((M // 2, M, L), np.complex128)
+    d = np.empty((G, M, M), np.complex128)
+    if _load().oracle_filter_frame(M, float(T), L, h, c, gamma, G, ax, ay, int(P), float(D), float(obstruction),
+                                   float(r0), float(L0), float(noise_level), int(key[0]) & 0xFFFFFFFF,
+                                   int(key[1]) & 0xFFFFFFFF, int(F), phi, d):
+        raise ValueError("oracle_filter_frame: bad arguments")
+    return phi, d
+
+
+def filter_frames_loss(M, T, h, c, gamma, ax, ay, B, P, D, obstruction, r0, L0, noise_level, key, frame0, nwrap,
+                       nframes):
     """(loss, energy) of reconstruction B [M][M][L][G] on the learned filter's
-    Fourier-domain training frames (layered model of Section 2)."""
+    training frames (frame0 + i) mod nwrap, i < nframes."""
     h, c, gamma, ax, ay = map(_f64, (h, c, gamma, ax, ay))
     B = _c128(B)
     L, G = len(h), len(ax)
     loss, energy = C.c_double(), C.c_double()
-    if _load().oracle_filter_frames_loss(M, float(T), L, h, c, gamma, G, ax, ay, B, float(r0), float(L0),
-                                         float(noise_level), int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF,
-                                         int(frame0), int(nwrap), int(nframes), C.byref(loss), C.byref(energy)):
+    if _load().oracle_filter_frames_loss(M, float(T), L, h, c, gamma, G, ax, ay, B, int(P), float(D),
+                                         float(obstruction), float(r0), float(L0), float(noise_level),
+                                         int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF, int(frame0),
+                                         int(nwrap), int(nframes), C.byref(loss), C.byref(energy)):
         raise ValueError("oracle_filter_frames_loss: bad arguments")
     return loss.value, energy.value
 

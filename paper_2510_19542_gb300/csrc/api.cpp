@@ -169,6 +169,8 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     p->precision = g->precision;
     p->output_metric = g->output_grid == SAFR_METRIC;
     p->delta = g->pitch_m;
+    p->diameter = g->diameter_m;
+    p->obstruction = g->obstruction;
     p->T = g->M * g->pitch_m / 2.0;
     p->beta = g->beta;
     p->h.assign(g->h_m, g->h_m + g->L);

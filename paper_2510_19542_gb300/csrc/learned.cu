@@ -394,17 +394,188 @@ __global__ void k_adam(float *master, float *m, float *v, const float *grad, __n
 }
 
 // ---------------------------------------------------------------------------
-// training frames: loss and its gradient with respect to the weights w
+// training frames: the layered model of Section 2 seen through the aperture,
+// and the loss with its gradient with respect to the weights w
 // ---------------------------------------------------------------------------
-constexpr int kFrameThreads = 256;  // frames per block (one block per frequency)
+constexpr int kFrameThreads = 256;  // frames per step (one thread per frame in the per-frequency kernels)
+
+// phi_l(n) of frame F at stored frequency (j, k), k < M/2: complex normal with
+// variance var, from the Box-Muller pair of Philox counter (F, k M + j, l, 0).
+// On the row k = 0 the frequencies j > M/2 are the conjugates of M - j, so
+// every layer is a real screen.
+__device__ __forceinline__ float2 layer_coeff(int M, int L, const float *var, uint32_t F, int j, int k, int l,
+                                              uint32_t k0, uint32_t k1)
+{
+    const bool flip = k == 0 && j > M / 2;
+    const int f = k * M + (flip ? M - j : j);
+    const float sd = sqrtf(0.5f * var[(size_t)f * L + l]);
+    const float2 z = normal2(F, (uint32_t)f, (uint32_t)l, 0u, k0, k1);
+    return make_float2(sd * z.x, flip ? -sd * z.y : sd * z.y);
+}
+
+struct CleanArgs {
+    int M, L, G, NF;
+    const float2 *E;          // [NF][G][L] e^{i theta_gl}
+    const float *var;         // [NF][L]
+    uint32_t k0, k1, frame0, nwrap;
+    float2 *c;                // [256][G][NF] noise-free data spectra
+};
+
+// One block per stored frequency, one thread per frame: c_g(n) = sum_l e^{i theta_gl(n)} phi_l(n).
+__global__ void __launch_bounds__(kFrameThreads) k_tf_clean(CleanArgs a)
+{
+    const int f = blockIdx.x, j = f % a.M, k = f / a.M, t = threadIdx.x;
+    const uint32_t F = (a.frame0 + (uint32_t)t) % a.nwrap;
+    float cr[SAFR_MAX_GROUP_G], ci[SAFR_MAX_GROUP_G];
+#pragma unroll
+    for (int g = 0; g < SAFR_MAX_GROUP_G; ++g) cr[g] = ci[g] = 0.0f;
+    if (j != a.M / 2) {
+        const float2 *E = a.E + (size_t)f * a.G * a.L;
+        for (int l = 0; l < a.L; ++l) {
+            const float2 p = layer_coeff(a.M, a.L, a.var, F, j, k, l, a.k0, a.k1);
+#pragma unroll
+            for (int g = 0; g < SAFR_MAX_GROUP_G; ++g)
+                if (g < a.G) {
+                    const float2 e = E[g * a.L + l];
+                    cr[g] += e.x * p.x - e.y * p.y;
+                    ci[g] += e.x * p.y + e.y * p.x;
+                }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < SAFR_MAX_GROUP_G; ++g)
+        if (g < a.G) a.c[((size_t)t * a.G + g) * a.NF + f] = make_float2(cr[g], ci[g]);
+}
+
+struct MaskArgs {
+    int M, G, NF;
+    const float2 *c;              // [256][G][NF]
+    const unsigned char *mask;    // [M][M] pupil on the grid (zero outside the P x P pupil square)
+    float noise;                  // per-pixel noise std / RMS of the noise-free wavefront over the mask
+    uint32_t k0, k1, frame0, nwrap;
+    float2 *d;                    // [256][G][NF] data spectra
+};
+
+constexpr int kMaskThreads = 256;
+constexpr int kMaxTrainM = 64;  // the direct DFTs of the aperture step hold two M x M complex tiles in shared memory
+
+// One block per (frame, star): psi = IDFT2(c) (a real field), psi <- mask (psi + noise), d = DFT2(psi).
+// The noise at grid pixel (p, q) is sigma z, z the first normal of Philox counter (F, p M + q, g, 1),
+// sigma = noise x RMS of the masked noise-free wavefront.  Direct DFTs (M <= 64), twiddles from a table
+// indexed by the exact residue (j p) mod M.
+__global__ void __launch_bounds__(kMaskThreads) k_tf_mask(MaskArgs a)
+{
+    extern __shared__ float2 sm2[];
+    const int M = a.M, MM = M * M, Mh = M / 2;
+    float2 *X = sm2, *Y = sm2 + MM, *tw = sm2 + 2 * MM;
+    float *red = (float *)(tw + M);
+    const int t = blockIdx.x / a.G, g = blockIdx.x % a.G;
+    const uint32_t F = (a.frame0 + (uint32_t)t) % a.nwrap;
+    const float2 *c = a.c + ((size_t)t * a.G + g) * a.NF;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        float s, co;
+        sincospif(2.0f * (float)i / (float)M, &s, &co);
+        tw[i] = make_float2(co, s);  // e^{+2 pi i i / M}
+    }
+    // full Hermitian spectrum X[j][k]
+    for (int i = threadIdx.x; i < MM; i += blockDim.x) {
+        const int j = i / M, k = i % M;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (k < Mh) v = c[k * M + j];
+        else if (k > Mh) {
+            const float2 u = c[(M - k) * M + (M - j) % M];
+            v = make_float2(u.x, -u.y);
+        }
+        X[i] = v;
+    }
+    __syncthreads();
+    // inverse along j: Y[p][k] = sum_j X[j][k] e^{+2 pi i j p / M}
+    for (int i = threadIdx.x; i < MM; i += blockDim.x) {
+        const int p = i / M, k = i % M;
+        float re = 0.0f, im = 0.0f;
+        for (int j = 0; j < M; ++j) {
+            const float2 x = X[j * M + k], w = tw[(j * p) % M];
+            re += x.x * w.x - x.y * w.y;
+            im += x.x * w.y + x.y * w.x;
+        }
+        Y[i] = make_float2(re, im);
+    }
+    __syncthreads();
+    // inverse along k, real part, 1/M^2; mask; sums for the RMS
+    const float inv = 1.0f / (float)MM;
+    float s2 = 0.0f, cnt = 0.0f;
+    for (int i = threadIdx.x; i < MM; i += blockDim.x) {
+        const int p = i / M, q = i % M;
+        float re = 0.0f;
+        for (int k = 0; k < M; ++k) {
+            const float2 y = Y[p * M + k], w = tw[(k * q) % M];
+            re += y.x * w.x - y.y * w.y;
+        }
+        const float m = a.mask[i] ? 1.0f : 0.0f;
+        const float v = m * re * inv;
+        X[i] = make_float2(v, m);
+        s2 += v * v;
+        cnt += m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[threadIdx.x >> 5] = s2;
+        red[8 + (threadIdx.x >> 5)] = cnt;
+    }
+    __syncthreads();
+    float S2 = 0.0f, N = 0.0f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        S2 += red[w];
+        N += red[8 + w];
+    }
+    const float sigma = N > 0.0f ? a.noise * sqrtf(S2 / N) : 0.0f;
+    // noise on the mask pixels, then forward along q for k < M/2: Y[p][k] = sum_q psi[p][q] e^{-2 pi i k q / M}
+    for (int i = threadIdx.x; i < MM; i += blockDim.x) {
+        const float2 v = X[i];
+        if (v.y != 0.0f && sigma > 0.0f) {
+            const float2 z = normal2(F, (uint32_t)i, (uint32_t)g, 1u, a.k0, a.k1);
+            X[i] = make_float2(v.x + sigma * z.x, v.y);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < M * Mh; i += blockDim.x) {
+        const int p = i / Mh, k = i % Mh;
+        float re = 0.0f, im = 0.0f;
+        for (int q = 0; q < M; ++q) {
+            const float x = X[p * M + q].x;
+            const float2 w = tw[(k * q) % M];
+            re += x * w.x;
+            im -= x * w.y;
+        }
+        Y[p * Mh + k] = make_float2(re, im);
+    }
+    __syncthreads();
+    // forward along p: d[k][j] = sum_p Y[p][k] e^{-2 pi i j p / M}
+    float2 *d = a.d + ((size_t)t * a.G + g) * a.NF;
+    for (int i = threadIdx.x; i < M * Mh; i += blockDim.x) {
+        const int k = i / M, j = i % M;
+        float re = 0.0f, im = 0.0f;
+        for (int p = 0; p < M; ++p) {
+            const float2 y = Y[p * Mh + k], w = tw[(j * p) % M];
+            re += y.x * w.x + y.y * w.y;
+            im += y.y * w.x - y.x * w.y;
+        }
+        d[k * M + j] = make_float2(re, im);
+    }
+}
+
+inline size_t mask_smem(int M) { return (size_t)(2 * M * M + M) * sizeof(float2) + 16 * sizeof(float); }
 
 struct FrameArgs {
     int M, L, G, NF;
     Basis bs;
     const float *w;           // [NP]
     uint32_t k0, k1;          // generator key
-    uint32_t frame0, nwrap;   // thread t draws frame (frame0 + t) mod nwrap
-    float noise_sd;           // standard deviation of the real and imaginary parts of eta_g(n)
+    uint32_t frame0, nwrap;   // thread t holds frame (frame0 + t) mod nwrap
+    const float2 *d;          // [256][G][NF] data spectra (k_tf_mask)
     float *gw;                // [NP] or null: sum over the block's frames of dLoss / dw
     float *loss, *energy;     // [NF]: sums over the block's frames of |error|^2 and |phi_l(n)|^2
 };
@@ -429,8 +600,9 @@ __device__ __forceinline__ void block_sum_g(float (&v)[SAFR_MAX_GROUP_G], int G,
     __syncthreads();
 }
 
-// One block per frequency f = k * M + j, one thread per frame.  The frequency's
-// weight in the full spectrum is 2 for k > 0 (its conjugate partner) and 1 for k = 0.
+// One block per stored frequency f = k * M + j, one thread per frame.  The frequency's
+// weight in the full spectrum is 2 for k > 0 (its conjugate partner) and 1 for k = 0
+// (both j and M - j are stored).
 __global__ void __launch_bounds__(kFrameThreads) k_filter_frames(FrameArgs a)
 {
     __shared__ float red[(kFrameThreads / 32) * SAFR_MAX_GROUP_G];
@@ -443,34 +615,19 @@ __global__ void __launch_bounds__(kFrameThreads) k_filter_frames(FrameArgs a)
     }
     const float wf = k == 0 ? 1.0f : 2.0f;
     const uint32_t F = (a.frame0 + (uint32_t)t) % a.nwrap;
-    const float2 *E = a.bs.E + (size_t)f * G * L;
     const double2 *U = a.bs.U + (size_t)f * G * G;
     const double2 *Q = a.bs.Q + (size_t)f * L * G;
-    const float *var = a.bs.var + (size_t)f * L;
     const float *w = a.w + (size_t)f * L * G;
-    // data d_g = sum_l e^{i theta_gl} phi_l + eta_g
     float dr[SAFR_MAX_GROUP_G], di[SAFR_MAX_GROUP_G];
 #pragma unroll
-    for (int g = 0; g < SAFR_MAX_GROUP_G; ++g) dr[g] = di[g] = 0.0f;
-    for (int l = 0; l < L; ++l) {
-        const float sd = sqrtf(0.5f * var[l]);
-        const float2 z = normal2(F, (uint32_t)f, (uint32_t)l, 0u, a.k0, a.k1);
-        const float pr = sd * z.x, pi = sd * z.y;
-#pragma unroll
-        for (int g = 0; g < SAFR_MAX_GROUP_G; ++g)
-            if (g < G) {
-                const float2 e = E[g * L + l];
-                dr[g] += e.x * pr - e.y * pi;
-                di[g] += e.x * pi + e.y * pr;
-            }
-    }
-#pragma unroll
-    for (int g = 0; g < SAFR_MAX_GROUP_G; ++g)
+    for (int g = 0; g < SAFR_MAX_GROUP_G; ++g) {
+        dr[g] = di[g] = 0.0f;
         if (g < G) {
-            const float2 z = normal2(F, (uint32_t)f, (uint32_t)(L + g), 0u, a.k0, a.k1);
-            dr[g] += a.noise_sd * z.x;
-            di[g] += a.noise_sd * z.y;
+            const float2 v = a.d[((size_t)t * G + g) * a.NF + f];
+            dr[g] = v.x;
+            di[g] = v.y;
         }
+    }
     // y_r = sum_g conj(U_gr) d_g
     float yr[SAFR_MAX_GROUP_G], yi[SAFR_MAX_GROUP_G];
 #pragma unroll
@@ -485,11 +642,9 @@ __global__ void __launch_bounds__(kFrameThreads) k_filter_frames(FrameArgs a)
     }
     float lsum = 0.0f, esum = 0.0f;
     for (int l = 0; l < L; ++l) {
-        const float sd = sqrtf(0.5f * var[l]);
-        const float2 z = normal2(F, (uint32_t)f, (uint32_t)l, 0u, a.k0, a.k1);
-        const float pr = sd * z.x, pi = sd * z.y;
+        const float2 ph = layer_coeff(a.M, L, a.bs.var, F, j, k, l, a.k0, a.k1);
         float qyr[SAFR_MAX_GROUP_G], qyi[SAFR_MAX_GROUP_G];
-        float er = -pr, ei = -pi;  // rec_l - phi_l, rec_l = sum_r Q_lr w_lr y_r
+        float er = -ph.x, ei = -ph.y;  // rec_l - phi_l, rec_l = sum_r Q_lr w_lr y_r
 #pragma unroll
         for (int r = 0; r < SAFR_MAX_GROUP_G; ++r) {
             qyr[r] = qyi[r] = 0.0f;
@@ -502,7 +657,7 @@ __global__ void __launch_bounds__(kFrameThreads) k_filter_frames(FrameArgs a)
             }
         }
         lsum += er * er + ei * ei;
-        esum += pr * pr + pi * pi;
+        esum += ph.x * ph.x + ph.y * ph.y;
         if (a.gw) {  // d|e|^2 / dw_lr = 2 Re(conj(e) Q_lr y_r)
             float gv[SAFR_MAX_GROUP_G];
 #pragma unroll
@@ -574,6 +729,8 @@ struct FilterState {
     float *hn = nullptr, *w = nullptr, *wplain = nullptr, *phi = nullptr, *act = nullptr, *gw = nullptr;
     float *partial = nullptr, *grad = nullptr, *master = nullptr, *m = nullptr, *v = nullptr;
     float *loss = nullptr, *energy = nullptr;
+    float2 *cbuf = nullptr, *dbuf = nullptr;  // [256][G][NF] noise-free and measured data spectra of a step
+    unsigned char *mask = nullptr;            // [M][M] pupil on the grid
     __nv_bfloat16 *wb = nullptr;
     int *flag = nullptr;
     bool basis_ready = false, training = false;
@@ -585,7 +742,7 @@ void filter_free(safr_plan_s *pl)
     if (!fs) return;
     void *bufs[] = {fs->bs.U, fs->bs.sig, fs->bs.Q, fs->bs.E, fs->bs.s, fs->bs.var, fs->hn, fs->w, fs->wplain,
                     fs->phi, fs->act, fs->gw, fs->partial, fs->grad, fs->master, fs->m, fs->v, fs->loss,
-                    fs->energy, fs->wb, fs->flag};
+                    fs->energy, fs->wb, fs->flag, fs->cbuf, fs->dbuf, fs->mask};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete fs;
@@ -641,7 +798,7 @@ safr_status filter_prepare(safr_plan_s *pl, bool training, cudaStream_t st)
     const int M = pl->M, Mh = pl->Mh, L = pl->L, G = pl->grp[0].G;
     fs->NF = M * Mh;
     fs->NP = fs->NF * L * G;
-    if (training && (size_t)fs->NP > kMaxTrainPoints) return SAFR_ERR_UNSUPPORTED_SIZE;
+    if (training && ((size_t)fs->NP > kMaxTrainPoints || M > safr::kMaxTrainM)) return SAFR_ERR_UNSUPPORTED_SIZE;
     if (!fs->bs.U) {
         fs->bs.NF = fs->NF;
         if (!dalloc(&fs->bs.U, (size_t)fs->NF * G * G) || !dalloc(&fs->bs.sig, (size_t)fs->NF * G) ||
@@ -662,12 +819,26 @@ safr_status filter_prepare(safr_plan_s *pl, bool training, cudaStream_t st)
             !dalloc(&fs->partial, (size_t)nblk * safr::kParams) || !dalloc(&fs->grad, (size_t)safr::kParams) ||
             !dalloc(&fs->master, (size_t)safr::kParams) || !dalloc(&fs->m, (size_t)safr::kParams) ||
             !dalloc(&fs->v, (size_t)safr::kParams) || !dalloc(&fs->loss, (size_t)fs->NF) ||
-            !dalloc(&fs->energy, (size_t)fs->NF))
+            !dalloc(&fs->energy, (size_t)fs->NF) ||
+            !dalloc(&fs->cbuf, (size_t)safr::kFrameThreads * G * fs->NF) ||
+            !dalloc(&fs->dbuf, (size_t)safr::kFrameThreads * G * fs->NF) || !dalloc(&fs->mask, (size_t)M * M))
             return SAFR_ERR_OOM;
+        // the pupil of the geometry (an annulus, or the whole P x P square) at offset (M - P) / 2
+        std::vector<unsigned char> mk((size_t)M * M, 0);
+        const int P = pl->P, o = (M - P) / 2;
+        const double ro = pl->diameter / 2.0, ri = pl->obstruction * pl->diameter / 2.0;
+        for (int a = 0; a < P; ++a)
+            for (int b = 0; b < P; ++b) {
+                const double x = (a - (P - 1) / 2.0) * pl->delta, y = (b - (P - 1) / 2.0) * pl->delta;
+                const double r2 = x * x + y * y;
+                mk[(size_t)(o + a) * M + o + b] = pl->diameter <= 0 ? 1 : (r2 <= ro * ro && r2 >= ri * ri);
+            }
+        if (cudaMemcpy(fs->mask, mk.data(), mk.size(), cudaMemcpyHostToDevice) != cudaSuccess) return SAFR_ERR_CUDA;
         fs->training = true;
     }
     if (!safr::smem_limit_allows((const void *)safr::k_mlp_forward, fwd_smem()) ||
-        !safr::smem_limit_allows((const void *)safr::k_mlp_backward, bwd_smem()))
+        !safr::smem_limit_allows((const void *)safr::k_mlp_backward, bwd_smem()) ||
+        (training && !safr::smem_limit_allows((const void *)safr::k_tf_mask, safr::mask_smem(M))))
         return SAFR_ERR_UNSUPPORTED_SIZE;
     if (!fs->basis_ready) {
         const safr::Group &g = pl->grp[0];
@@ -816,15 +987,29 @@ double layer_variance(const safr_plan_s *pl, int l, int j, int k, double r0, dou
     return m2 * m2 * 0.5 * psd / (period * period);
 }
 
+// The data spectra of the 256 frames (frame0 + t) mod nwrap, t < 256, drawn with key (k0, k1).
+cudaError_t make_frames(safr_plan_s *pl, FilterState *fs, uint32_t k0, uint32_t k1, uint32_t frame0, uint32_t nwrap,
+                        double noise, cudaStream_t st)
+{
+    const int G = pl->grp[0].G;
+    safr::CleanArgs ca{pl->M, pl->L, G, fs->NF, fs->bs.E, fs->bs.var, k0, k1, frame0, nwrap, fs->cbuf};
+    safr::k_tf_clean<<<fs->NF, safr::kFrameThreads, 0, st>>>(ca);
+    safr::MaskArgs ma{pl->M, G, fs->NF, fs->cbuf, fs->mask, (float)noise, k0, k1, frame0, nwrap, fs->dbuf};
+    safr::k_tf_mask<<<safr::kFrameThreads * G, safr::kMaskThreads, safr::mask_smem(pl->M), st>>>(ma);
+    return cudaGetLastError();
+}
+
 // Sum of loss and energy over nframes frames (chunks of kFrameThreads) drawn with
 // key (k0, k1) for weights w.
 bool eval_frames(safr_plan_s *pl, FilterState *fs, const float *w, uint32_t k0, uint32_t k1, uint32_t frame0,
-                 uint32_t nwrap, int nframes, float noise_sd, double &loss, double &energy, cudaStream_t st)
+                 uint32_t nwrap, int nframes, double noise, double &loss, double &energy, cudaStream_t st)
 {
     loss = energy = 0;
     for (int c = 0; c < nframes; c += safr::kFrameThreads) {
-        safr::FrameArgs fa{pl->M, pl->L, pl->grp[0].G, fs->NF, fs->bs, w, k0, k1,
-                           (uint32_t)((frame0 + (uint32_t)c) % nwrap), nwrap, noise_sd, nullptr, fs->loss, fs->energy};
+        const uint32_t f0 = (uint32_t)((frame0 + (uint32_t)c) % nwrap);
+        if (make_frames(pl, fs, k0, k1, f0, nwrap, noise, st) != cudaSuccess) return false;
+        safr::FrameArgs fa{pl->M, pl->L, pl->grp[0].G, fs->NF, fs->bs, w, k0, k1, f0, nwrap, fs->dbuf, nullptr,
+                           fs->loss, fs->energy};
         safr::k_filter_frames<<<fs->NF, safr::kFrameThreads, 0, st>>>(fa);
         if (cudaGetLastError() != cudaSuccess) return false;
         double a, b;
@@ -864,7 +1049,6 @@ extern "C" safr_status safr_filter_train(safr_plan_t pl, const safr_filter_confi
                 Ef += (k == 0 ? 1.0 : 2.0) * v;
             }
     if (!(Ef > 0)) return SAFR_ERR_INVALID_ARG;
-    const float noise_sd = (float)std::sqrt(cfg->noise_level * cfg->noise_level * Ef / ((double)M * M) / 2.0);
 
     // initial weights: N(0, 1 / fan_in), zero biases
     std::vector<float> w0(safr::kParams, 0.0f);
@@ -899,7 +1083,7 @@ extern "C" safr_status safr_filter_train(safr_plan_t pl, const safr_filter_confi
 
     // training loss on the first frames before training
     if (mlp_forward(pl, fs, cfg->noise_level, fs->w, nullptr, nullptr, st) != cudaSuccess ||
-        !eval_frames(pl, fs, fs->w, k0, k1, 0, ntrain, probe, noise_sd, l_a, e_a, st))
+        !eval_frames(pl, fs, fs->w, k0, k1, 0, ntrain, probe, cfg->noise_level, l_a, e_a, st))
         return SAFR_ERR_CUDA;
     const double first = l_a / e_a;
 
@@ -912,7 +1096,8 @@ extern "C" safr_status safr_filter_train(safr_plan_t pl, const safr_filter_confi
     for (long it = 0; it < steps; ++it) {
         const uint32_t frame0 = (uint32_t)(((uint64_t)(it % steps_per_epoch) * T) % ntrain);
         if (mlp_forward(pl, fs, cfg->noise_level, fs->w, fs->phi, fs->act, st) != cudaSuccess) return SAFR_ERR_CUDA;
-        safr::FrameArgs fa{M, L, G, NF, fs->bs, fs->w, k0, k1, frame0, ntrain, noise_sd, fs->gw, fs->loss, fs->energy};
+        if (make_frames(pl, fs, k0, k1, frame0, ntrain, cfg->noise_level, st) != cudaSuccess) return SAFR_ERR_CUDA;
+        safr::FrameArgs fa{M, L, G, NF, fs->bs, fs->w, k0, k1, frame0, ntrain, fs->dbuf, fs->gw, fs->loss, fs->energy};
         safr::k_filter_frames<<<NF, T, 0, st>>>(fa);
         safr::MlpBackArgs ba{M,  L,      G,      NP,      fs->wb, fs->bs.sig, fs->hn, (float)(cfg->noise_level / 0.05),
                              fs->act, fs->phi, fs->gw, fs->partial};
@@ -930,10 +1115,10 @@ extern "C" safr_status safr_filter_train(safr_plan_t pl, const safr_filter_confi
     double lv_learned, ev, lv_plain, ev2;
     int flag = 0;
     if (mlp_forward(pl, fs, cfg->noise_level, fs->w, nullptr, nullptr, st) != cudaSuccess ||
-        !eval_frames(pl, fs, fs->w, k0, k1, 0, ntrain, probe, noise_sd, l_a, e_a, st) ||
-        !eval_frames(pl, fs, fs->w, v0, v1, 0, (uint32_t)cfg->valid_frames, cfg->valid_frames, noise_sd, lv_learned,
+        !eval_frames(pl, fs, fs->w, k0, k1, 0, ntrain, probe, cfg->noise_level, l_a, e_a, st) ||
+        !eval_frames(pl, fs, fs->w, v0, v1, 0, (uint32_t)cfg->valid_frames, cfg->valid_frames, cfg->noise_level, lv_learned,
                      ev, st) ||
-        !eval_frames(pl, fs, fs->wplain, v0, v1, 0, (uint32_t)cfg->valid_frames, cfg->valid_frames, noise_sd,
+        !eval_frames(pl, fs, fs->wplain, v0, v1, 0, (uint32_t)cfg->valid_frames, cfg->valid_frames, cfg->noise_level,
                      lv_plain, ev2, st) ||
         cudaMemcpyAsync(&flag, fs->flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -961,7 +1146,6 @@ extern "C" safr_status safr_filter_train(safr_plan_t pl, const safr_filter_confi
         res->steps = steps;
         res->used_learned = use ? 1 : 0;
         res->nonfinite = flag;
-        res->noise_sd = noise_sd;
     }
     return cudaStreamSynchronize(st) == cudaSuccess ? SAFR_OK : SAFR_ERR_CUDA;
 }

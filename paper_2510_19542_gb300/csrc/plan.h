@@ -82,6 +82,7 @@ struct safr_plan_s {
     int M = 0, P = 0, L = 0, G = 0, Mh = 0, o = 0;
     int precision = SAFR_FP32, output_metric = 0, mixed = 0, remove_tt = 0;
     double delta = 0, T = 0, beta = 0;
+    double diameter = 0, obstruction = 0;  // pupil annulus (diameter <= 0: the whole P x P square)
     std::vector<double> h, gamma;
     int ngroups = 0;
     safr::Group grp[2];

@@ -74,7 +74,7 @@ class safr_filter_config(C.Structure):
 class safr_filter_result(C.Structure):
     _fields_ = [("train_loss_first", C.c_double), ("train_loss_last", C.c_double),
                 ("valid_loss_learned", C.c_double), ("valid_loss_plain", C.c_double), ("steps", C.c_long),
-                ("used_learned", C.c_int), ("nonfinite", C.c_int), ("noise_sd", C.c_double)]
+                ("used_learned", C.c_int), ("nonfinite", C.c_int)]
 
 
 _lib = None

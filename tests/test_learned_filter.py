@@ -5,8 +5,8 @@ BF16, so both sides use identical values) against the oracle's
 group_B_learned; the MLP runs in FP32 on the GPU and B is stored in FP32, so
 the bar is a max error of 2e-5 of max|B|.  Training: the held-out error of
 plain SAFR that safr_filter_train reports is recomputed by the oracle on the
-same Philox frames (relative 1e-4), and so is the learned filter's, from the
-parameters the call returns.  The fallback: non-finite MLP output or a learned
+same Philox frames, built through the pupil (relative 1e-4), and so is the
+learned filter's, from the parameters the call returns.  The fallback: non-finite MLP output or a learned
 filter that does not beat plain SAFR leaves plain SAFR's B in the plan.
 """
 import math
@@ -70,8 +70,9 @@ def as_gpu_layout(Bo):
 
 def frames_loss(oracle_mod, g, B, r0, L0, noise, key, nframes):
     a = oracle_args(g)
-    return oracle_mod.filter_frames_loss(a["M"], a["T"], a["h"], a["c"], a["gamma"], a["ax"], a["ay"], B, r0, L0,
-                                         noise, key, 0, nframes, nframes)
+    return oracle_mod.filter_frames_loss(a["M"], a["T"], a["h"], a["c"], a["gamma"], a["ax"], a["ay"], B, g["P"],
+                                         g.get("diameter", 0.0), g.get("obstruction", 0.0), r0, L0, noise, key, 0,
+                                         nframes, nframes)
 
 
 def test_apply_matches_oracle(safr, synth, oracle_mod):

@@ -154,9 +154,15 @@ def test_learned_B_feature_dependence(oracle_mod, q):
         assert np.max(np.abs(B[j, k] - ref)) <= 1e-10 * np.max(np.abs(ref)), (j, k)
 
 
-def _frames_loss(oracle_mod, g, B, noise, nframes, key=(11, 22)):
-    return oracle_mod.filter_frames_loss(g["M"], g["T"], g["h"], g["c"], g["gamma"], g["ax"], g["ay"], B, 0.15,
-                                         25.0, noise, key, 0, 1 << 20, nframes)
+def _frames_loss(oracle_mod, g, B, noise, nframes, key=(11, 22), P=None, D=0.0, obstruction=0.0):
+    """Loss over nframes training frames; by default no aperture (P = M, D = 0)."""
+    return oracle_mod.filter_frames_loss(g["M"], g["T"], g["h"], g["c"], g["gamma"], g["ax"], g["ay"], B,
+                                         P or g["M"], D, obstruction, 0.15, 25.0, noise, key, 0, 1 << 20, nframes)
+
+
+def _frame(oracle_mod, g, F, noise, P=None, D=0.0, obstruction=0.0, key=(5, 6)):
+    return oracle_mod.filter_frame(g["M"], g["T"], g["h"], g["c"], g["gamma"], g["ax"], g["ay"], P or g["M"], D,
+                                   obstruction, 0.15, 25.0, noise, key, F)
 
 
 def test_frames_zero_reconstruction_loses_all_energy(oracle_mod):
@@ -215,3 +221,83 @@ def test_frames_energy_and_noise_statistics(oracle_mod):
             fro += (1 if k == 0 else 2) * np.sum(abs(B[j, k]) ** 2)
     expect = nu ** 2 * Ef / M ** 2 * fro
     assert abs(loss / nf / expect - 1) < 0.05
+
+
+def test_frame_layers_are_real_screens(oracle_mod):
+    """phi_l(-n) = conj(phi_l(n)) on the stored row k = 0; nothing at n = 0 or on the Nyquist row."""
+    g = _geometry(3, 4, M=16, seed=8)
+    phi, _ = _frame(oracle_mod, g, 3, 0.0)
+    M = g["M"]
+    for j in range(1, M // 2):
+        assert np.array_equal(phi[0, M - j], phi[0, j].conj())
+    assert np.all(phi[0, 0] == 0) and np.all(phi[:, M // 2] == 0)
+    assert np.all(np.abs(phi[1:, 1]) > 0)
+
+
+def test_frame_data_without_aperture_is_the_layered_model(oracle_mod):
+    """No aperture, no noise: d_g(n) = sum_l exp(i pi n.(alpha_g h_l) / (c_l T)) phi_l(n)
+    (Section 2 in the Fourier domain) and the wavefront numpy's ifft2 gives is real."""
+    g = _geometry(3, 4, M=16, seed=9)
+    M = g["M"]
+    phi, d = _frame(oracle_mod, g, 7, 0.0)
+    for j in range(M):
+        for k in range(1, M // 2):
+            if j == M // 2:
+                continue
+            s, A = _A(g, j, k)
+            ref = (A / s[None, :]) @ phi[k, j]
+            assert np.max(np.abs(d[:, j, k] - ref)) <= 1e-9 * np.max(np.abs(ref))
+    for gi in range(3):
+        w = np.fft.ifft2(d[gi])
+        assert np.max(np.abs(w.imag)) <= 1e-12 * np.max(np.abs(w.real))
+
+
+def test_frame_aperture_and_noise(oracle_mod):
+    """With a pupil (P < M, annulus of diameter D): numpy's ifft2 of d is real,
+    zero off the pupil (the mask of synth.pupil placed at (M-P)/2), and equals
+    the aperture-free wavefront on it.  With noise, the difference is white
+    noise on the pupil only, of std noise x RMS of the noise-free wavefront."""
+    from paper_2510_19542_gb300 import synth
+    g = _geometry(3, 4, M=32, seed=10)
+    M, P, D, obs = g["M"], 28, 6.5, 0.1
+    pitch = 2 * g["T"] / M
+    pm = synth.pupil(dict(P=P, pitch=pitch, diameter=D, obstruction=obs))
+    mask = np.zeros((M, M), bool)
+    o = (M - P) // 2
+    mask[o:o + P, o:o + P] = pm
+    _, d_free = _frame(oracle_mod, g, 4, 0.0)
+    _, d_clean = _frame(oracle_mod, g, 4, 0.0, P=P, D=D, obstruction=obs)
+    _, d_noisy = _frame(oracle_mod, g, 4, 0.2, P=P, D=D, obstruction=obs)
+    for gi in range(3):
+        free = np.fft.ifft2(d_free[gi]).real
+        clean = np.fft.ifft2(d_clean[gi])
+        noisy = np.fft.ifft2(d_noisy[gi])
+        scale = np.max(np.abs(free))
+        assert np.max(np.abs(clean.imag)) <= 1e-12 * scale and np.max(np.abs(noisy.imag)) <= 1e-12 * scale
+        assert np.max(np.abs(clean.real - free * mask)) <= 1e-12 * scale
+        eta = noisy.real - clean.real
+        assert np.max(np.abs(eta[~mask])) <= 1e-12 * scale
+        rms = np.sqrt(np.mean(free[mask] ** 2))
+        assert abs(np.std(eta[mask]) / rms / 0.2 - 1) < 0.1
+        assert abs(np.mean(eta[mask])) < 0.15 * 0.2 * rms
+
+
+def test_frames_loss_sums_the_frames(oracle_mod):
+    """The loss of two frames is the weighted squared error of B d against phi
+    over the stored frequencies (k = 0 weight 1, k > 0 weight 2, no Nyquist row)."""
+    g = _geometry(3, 4, M=16, seed=11)
+    M = g["M"]
+    B = _learned(oracle_mod, g, _one_path(2), 0.01)
+    loss, energy = _frames_loss(oracle_mod, g, B, 0.05, 2, key=(5, 6), P=14, D=3.5)
+    tl = te = 0.0
+    for F in range(2):
+        phi, d = _frame(oracle_mod, g, F, 0.05, P=14, D=3.5)
+        for k in range(M // 2):
+            for j in range(M):
+                if j == M // 2:
+                    continue
+                wn = 1 if k == 0 else 2
+                e = B[j, k] @ d[:, j, k] - phi[k, j]
+                tl += wn * np.sum(abs(e) ** 2)
+                te += wn * np.sum(abs(phi[k, j]) ** 2)
+    assert abs(loss / tl - 1) < 1e-12 and abs(energy / te - 1) < 1e-12
