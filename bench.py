@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "passes"])
-    ap.add_argument("--no-workloads", action="store_true", help="skip the 32-grid, 512-grid, batched and learned-filter workloads")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the 32-grid, 512-grid, batched, learned-filter and loop-step workloads")
     return ap.parse_args()
 
 
@@ -311,6 +311,56 @@ def measure_batch(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm,
     return "batched-64-uneven", out
 
 
+def measure_loop(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm):
+    """One AO-loop iteration of Algorithm 3 around SAFR on the MORFEO-like
+    geometry: POLC of the wavefronts with the mirror/layer state, the SAFR frame
+    (LGS tip/tilt removal included), and the integrator (gain 0.5), through
+    safr_loop_step; beside it each step alone.  L2 flushed before every call."""
+    g = synth.config(2)
+    plan = safr.Plan(g, device=dev.index)
+    info = plan.info
+    L, M, G, P = info["L"], info["M"], info["G"], info["P"]
+    x = torch.from_numpy(synth.frame(g, seed=700).astype(np.float32)).to(dev)
+    a = torch.zeros((L, M, M), dtype=torch.float32, device=dev)
+    tmp = torch.empty((G, P, P), dtype=torch.float32, device=dev)
+    phi = plan.empty_layers().zero_()
+
+    def timed(fn, i):
+        flush_l2(i)
+        s0 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        fn()
+        e0.record(stream)
+        e0.synchronize()
+        return s0.elapsed_time(e0)
+
+    step = lambda: safr.safr_loop_step(plan.handle, x, a, 0.5, stream=stream)  # noqa: E731
+    polc = lambda: safr.safr_polc(plan.handle, x, a, tmp, stream=stream)  # noqa: E731
+    integ = lambda: safr.safr_integrate(plan.handle, phi, a, 0.5, stream=stream)  # noqa: E731
+    for i in range(warmup):
+        timed(step, i)
+    lat = sorted(timed(step, i) for i in range(steps))
+    t_polc = float(np.median([timed(polc, i) for i in range(20)]))
+    t_int = float(np.median([timed(integ, i) for i in range(20)]))
+    status = safr.safr_get_status(plan.handle)
+    nbytes = M * (M // 2) * L * G * 8 + G * P * P * 4 + 2 * L * M * M * 4  # B, wavefronts, state read + write
+    mean_ms = float(np.mean(lat))
+    out = {"grid": M, "pupil": P, "stars": G, "layers": L, "precision": "fp32", "gain": 0.5,
+           "frames_per_s": 1e3 / mean_ms,
+           "latency_ms": {"p50": lat[len(lat) // 2],
+                          "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
+           "launches_per_step": 1 + safr.safr_launches_per_frame(plan.handle) + (
+               0 if safr.safr_get_path(plan.handle) == safr.SAFR_PATH_FUSED else 1),
+           "integrator": "fused into the frame kernel's store" if safr.safr_get_path(plan.handle) ==
+           safr.SAFR_PATH_FUSED else "separate kernel",
+           "polc_ms": t_polc, "integrate_ms": t_int,
+           "algorithmic_bytes": nbytes, "frac_of_hbm": nbytes / (mean_ms * 1e-3) / 1e9 / hbm,
+           "device_status": status, "steps": steps}
+    plan.close()
+    return "loop-step-morfeo-256", out
+
+
 def measure_learned(safr, synth, torch, dev, stream, steps, warmup, flush_l2):
     """The learned spectral filter on the 32-grid geometry with 35 layers: GPU
     training on 100k forward-model frames (2 epochs), the held-out comparison
@@ -533,6 +583,8 @@ def run_safr(args):
         name, res = measure_batch(safr, synth, torch, dev, stream, min(args.steps, 20), 3, flush_l2, hbm_pk)
         workloads[name] = res
         name, res = measure_learned(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2)
+        workloads[name] = res
+        name, res = measure_loop(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2, hbm_pk)
         workloads[name] = res
 
     if rank == 0:

@@ -432,6 +432,40 @@ safr_status safr_filter_train(safr_plan_t plan, const safr_filter_config *cfg, f
 safr_status safr_filter_apply(safr_plan_t plan, const float *weights, double noise_level, cudaStream_t stream);
 safr_status safr_filter_reset(safr_plan_t plan, cudaStream_t stream);
 
+/*
+ * The steps of the three-step AO loop around SAFR (Algorithm 3): pseudo open
+ * loop control (line 2) and the integrator (line 5).  The mirror/layer state
+ * a is L layers on the plan's output grid, [L][M][M] in the plan's precision
+ * (FP32 or FP64; plans with FP16 storage return SAFR_ERR_UNSUPPORTED_SIZE),
+ * the same layout safr_reconstruct writes.  Wavefront reconstruction from
+ * sensor data (CuReD) and the two-step delay of the loop are the caller's.
+ *
+ * safr_polc: psi~_g = psi_g + A_g a on the pupil, zero off it (the zero
+ * extension of Section 2), with the tomography operator of Section 2,
+ * (A_g a)(r) = sum_l a_l(c_l r + alpha_g h_l), evaluated matrix-free by
+ * bilinear interpolation of the layer samples (the O(N) evaluation of the
+ * paper's cost analysis).  For star g, layer l and pupil pixel (p, q) the
+ * sample point in output-grid pixels is, per axis,
+ *   native output grid:  u = o + p + s_gl
+ *   metric output grid:  u = M/2 + c_l (o + p - M/2 + s_gl)
+ * with s_gl = alpha_g h_l / (c_l delta), o = (M - P)/2, wrapped periodically
+ * onto [0, M).  d_wavefronts and d_out are [G][P][P] (geometry star order)
+ * and may not overlap d_a; d_out may equal d_wavefronts.
+ *
+ * safr_integrate: a <- (1 - gain) a + gain Phi over the L M^2 samples,
+ * 0 <= gain <= 1.
+ *
+ * safr_loop_step: one loop iteration on the plan's staging buffers: POLC of
+ * d_wavefronts with the current state d_a, SAFR (safr_reconstruct, with the
+ * LGS tip/tilt removal of a mixed plan), then the integrator into d_a.
+ * All three are asynchronous on `stream` and launch kernels only.
+ */
+safr_status safr_polc(safr_plan_t plan, const void *d_wavefronts, const void *d_a, void *d_out,
+                      cudaStream_t stream);
+safr_status safr_integrate(safr_plan_t plan, const void *d_layers, void *d_a, double gain, cudaStream_t stream);
+safr_status safr_loop_step(safr_plan_t plan, const void *d_wavefronts, void *d_a, double gain,
+                           cudaStream_t stream);
+
 /* Free every device and host resource of the plan (synchronises its device). */
 safr_status safr_destroy(safr_plan_t plan);
 

@@ -19,6 +19,8 @@ from .safr_oracle import (  # noqa: F401
     philox4x32_10,
     filter_frames_loss,
     filter_frame,
+    polc,
+    integrate,
     MLP_PARAMS,
     cone,
     remove_tt,

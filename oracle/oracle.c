@@ -868,3 +868,60 @@ int oracle_filter_frames_loss(int M, double T, int L, const double *h, const dou
     *energy = te;
     return 0;
 }
+
+/* ------------------------------------------------------------------------- */
+/* Pseudo open loop control (Algorithm 3, line 2) and the integrator (line 5). */
+/* POLC: out_g = mask (psi_g + A_g a), (A_g a)(r) = sum_l a_l(c_l r + alpha_g h_l) */
+/* (Eq. defAperonly), at the pupil sample r = delta (o + p - M/2) per axis     */
+/* (o = (M - P)/2), the layers a_l known at the output-grid samples: metric    */
+/* grid x = delta (u - M/2), native grid x = c_l delta (u - M/2), periodic     */
+/* with M samples, interpolated bilinearly between the four neighbours.        */
+/* Integrator: a <- (1 - gain) a + gain phi.                                    */
+/* ------------------------------------------------------------------------- */
+static double bilinear_periodic(const double *a, int M, double u, double v)
+{
+    double fu = floor(u), fv = floor(v);
+    double wu = u - fu, wv = v - fv;
+    long i0 = ((long)fu % M + M) % M, j0 = ((long)fv % M + M) % M;
+    long i1 = (i0 + 1) % M, j1 = (j0 + 1) % M;
+    return (1 - wu) * ((1 - wv) * a[i0 * M + j0] + wv * a[i0 * M + j1]) +
+           wu * ((1 - wv) * a[i1 * M + j0] + wv * a[i1 * M + j1]);
+}
+
+int oracle_polc(int M, int P, double delta, double D, double obstruction, int L, const double *h, int G,
+                const double *ax, const double *ay, const int *kind, double h_lgs, int output_metric,
+                const double *psi, const double *a, double *out)
+{
+    if (M <= 0 || P <= 0 || P > M || L <= 0 || G <= 0) return -1;
+    unsigned char *mask = (unsigned char *)malloc((size_t)P * P);
+    oracle_pupil_mask(P, delta, D, obstruction, mask);
+    const int o = (M - P) / 2;
+    double *c = (double *)malloc(sizeof(double) * L);
+    for (int g = 0; g < G; ++g) {
+        oracle_cone(L, h, h_lgs, kind[g] == 1, c);
+        for (int p = 0; p < P; ++p)
+            for (int q = 0; q < P; ++q) {
+                size_t i = ((size_t)g * P + p) * P + q;
+                if (!mask[p * P + q]) {
+                    out[i] = 0.0;
+                    continue;
+                }
+                double rx = delta * (o + p - M / 2.0), ry = delta * (o + q - M / 2.0);
+                double acc = psi[i];
+                for (int l = 0; l < L; ++l) {
+                    double X = c[l] * rx + ax[g] * h[l], Y = c[l] * ry + ay[g] * h[l];
+                    double pitch = output_metric ? delta : c[l] * delta;
+                    acc += bilinear_periodic(a + (size_t)l * M * M, M, M / 2.0 + X / pitch, M / 2.0 + Y / pitch);
+                }
+                out[i] = acc;
+            }
+    }
+    free(mask);
+    free(c);
+    return 0;
+}
+
+void oracle_integrate(long n, const double *phi, double *a, double gain)
+{
+    for (long i = 0; i < n; ++i) a[i] = (1.0 - gain) * a[i] + gain * phi[i];
+}

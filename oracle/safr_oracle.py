@@ -74,6 +74,9 @@ def _load():
                                                   _cp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                                                   C.c_double, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                                                   C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.oracle_polc.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_int, _dp, C.c_int,
+                                    _dp, _dp, _ip, C.c_double, C.c_int, _dp, _dp, _dp]
+        lib.oracle_integrate.argtypes = [C.c_long, _dp, _dp, C.c_double]
         lib.oracle_filter_frame.argtypes = [C.c_int, C.c_double, C.c_int, _dp, _dp, _dp, C.c_int, _dp, _dp,
                                             C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
                                             C.c_uint32, C.c_uint32, C.c_uint32, _cp, _cp]
@@ -200,6 +203,31 @@ def filter_frames_loss(M, T, h, c, gamma, ax, ay, B, P, D, obstruction, r0, L0, 
                                          int(nwrap), int(nframes), C.byref(loss), C.byref(energy)):
         raise ValueError("oracle_filter_frames_loss: bad arguments")
     return loss.value, energy.value
+
+
+def polc(geom: dict, wavefronts: np.ndarray, a: np.ndarray) -> np.ndarray:
+    """Pseudo open loop data (Algorithm 3, line 2): mask * (wavefronts + A(a)),
+    A the tomography operator of Section 2 on the bilinearly interpolated layers
+    a [L][M][M] of the plan's output grid (metric unless output_metric is 0)."""
+    g = geom
+    M, P = int(g["M"]), int(g["P"])
+    L, G = len(g["h"]), len(g["dir_x"])
+    psi = _f64(wavefronts).reshape(G, P, P)
+    a = _f64(a).reshape(L, M, M)
+    out = np.empty((G, P, P), np.float64)
+    if _load().oracle_polc(M, P, float(g["pitch"]), float(g.get("diameter", 0.0)), float(g.get("obstruction", 0.0)),
+                           L, _f64(g["h"]), G, _f64(g["dir_x"]), _f64(g["dir_y"]),
+                           np.ascontiguousarray(g["kind"], dtype=np.int32), float(g.get("h_lgs", 90e3)),
+                           int(g.get("output_metric", 1)), psi, a, out):
+        raise ValueError("oracle_polc: bad arguments")
+    return out
+
+
+def integrate(phi: np.ndarray, a: np.ndarray, gain: float) -> np.ndarray:
+    """Integrator (Algorithm 3, line 5): returns (1 - gain) a + gain phi."""
+    out = _f64(a).copy()
+    _load().oracle_integrate(out.size, _f64(phi).reshape(-1), out.reshape(-1), float(gain))
+    return out
 
 
 def pupil_mask(P: int, delta: float, D: float, obstruction: float) -> np.ndarray:

@@ -45,7 +45,7 @@ void free_plan_memory(safr_plan_s *p)
     void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask, p->d_tt_w,
                     p->d_xy_hat, p->d_pm, p->d_bar, p->d_stamps, p->d_twq,
                     p->d_pre, p->d_status, p->d_in_stage, p->d_out_stage, p->d_in_scales_stage,
-                    p->d_out_scales_stage};
+                    p->d_out_scales_stage, p->d_polc};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &e : p->ev)
@@ -312,6 +312,11 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
         SAFR_TRY(upload((float **)&p->d_rs_w, ff));
     }
     SAFR_TRY(upload(&p->d_mask, mask));
+    {  // sample points of the POLC operator (loop.cu)
+        std::vector<unsigned char> tab;
+        safr::polc_table(p, tab);
+        SAFR_TRY(upload(&p->d_polc, tab));
+    }
     if (p->precision == SAFR_FP64) {
         SAFR_TRY(upload((double **)&p->d_tt_w, ttw));
     } else {

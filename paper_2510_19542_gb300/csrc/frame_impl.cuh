@@ -73,6 +73,8 @@ struct Frame2Params {
     int skip_cta;              // test hook (-1: none)
     unsigned long long timeout_ns;
     R inv_M2;
+    int blend;                 // 1: out <- (1 - gain) out + gain layers (the AO loop's integrator)
+    R gain;
     // shared-memory carve-up (bytes from the dynamic base)
     unsigned off_rs, off_tw, off_b, off_d, off_xy, off_s3;
     const void *in;
@@ -724,10 +726,13 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                     const C zz = Z[(size_t)(npair0 + (r >> 1)) * M + q];
                     v += (r & 1) ? zz.y : zz.x;
                 }
+                R val = v * f;
+                if constexpr (!std::is_same<TOUT, __half>::value)
+                    if (fp.blend) val = (R(1) - fp.gain) * (R)outp[idx] + fp.gain * val;
                 if constexpr (std::is_same<TOUT, double>::value)
-                    store_out_d(outp + idx, (double)(v * f));
+                    store_out_d(outp + idx, (double)val);
                 else
-                    store_out<TOUT>(outp + idx, (float)(v * f));
+                    store_out<TOUT>(outp + idx, (float)val);
             }
             __syncthreads();
             SAFR_MARK(21, it == b);
@@ -893,6 +898,8 @@ struct Frame2Host {
         fp.skip_cta = pl->debug_skip_cta;
         fp.timeout_ns = pl->barrier_timeout_ns;
         fp.inv_M2 = (R)(1.0 / ((double)M * M));
+        fp.blend = pl->loop_blend;
+        fp.gain = (R)pl->loop_gain;
         fp.off_rs = pl->f2_off_rs;
         fp.off_tw = pl->f2_off_tw;
         fp.off_b = pl->f2_off_b;

@@ -126,6 +126,9 @@ struct safr_plan_s {
     unsigned long long *d_bar = nullptr; // grid barrier: arrival count, launch epoch
     unsigned long long *d_stamps = nullptr;  // [grid][SAFR_TRACE_MARKS] timestamps of traced fused frames
     double *d_pre = nullptr;  // shifts, sw, tau of both groups (precompute)
+    unsigned char *d_polc = nullptr;  // POLC sample points on the output grid and the pupil (loop.cu)
+    int loop_blend = 0;       // set by safr_loop_step around its persistent-kernel launch
+    double loop_gain = 0;     // integrator gain of that launch
     int *d_status = nullptr;
     void *d_in_stage = nullptr, *d_out_stage = nullptr;
     float *d_in_scales_stage = nullptr, *d_out_scales_stage = nullptr;
@@ -153,6 +156,7 @@ cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scal
                          cudaStream_t stream);
 void frame2_twiddles(int M, std::vector<double> &re, std::vector<double> &im);
 void filter_free(safr_plan_s *plan);
+void polc_table(const safr_plan_s *plan, std::vector<unsigned char> &bytes);
 inline bool use_fused(const safr_plan_s *plan)
 {
     return plan->fused_ok && plan->path != SAFR_PATH_PASSES;

@@ -38,7 +38,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc", "safr_autotune",
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
-            "safr_filter_reset"]
+            "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -123,6 +123,9 @@ def load(build_if_missing: bool = True):
                                       C.POINTER(safr_filter_result), vp]
     lib.safr_filter_apply.argtypes = [vp, C.POINTER(C.c_float), C.c_double, vp]
     lib.safr_filter_reset.argtypes = [vp, vp]
+    lib.safr_polc.argtypes = [vp, vp, vp, vp, vp]
+    lib.safr_integrate.argtypes = [vp, vp, vp, C.c_double, vp]
+    lib.safr_loop_step.argtypes = [vp, vp, vp, C.c_double, vp]
     lib.safr_status_string.argtypes = [C.c_int]
     lib.safr_status_string.restype = C.c_char_p
     for name in _EXPORTS:
@@ -310,6 +313,21 @@ def safr_filter_apply(plan: int, weights, noise_level: float, stream=None):
 
 def safr_filter_reset(plan: int, stream=None):
     _check(load().safr_filter_reset(plan, _stream(stream)), "safr_filter_reset")
+
+
+def safr_polc(plan: int, wavefronts, a, out, stream=None):
+    """Pseudo open loop data: out = mask * (wavefronts + A(a)) (device buffers)."""
+    _check(load().safr_polc(plan, _ptr(wavefronts), _ptr(a), _ptr(out), _stream(stream)), "safr_polc")
+
+
+def safr_integrate(plan: int, layers, a, gain: float, stream=None):
+    """Integrator: a <- (1 - gain) a + gain layers (device buffers, in place on a)."""
+    _check(load().safr_integrate(plan, _ptr(layers), _ptr(a), float(gain), _stream(stream)), "safr_integrate")
+
+
+def safr_loop_step(plan: int, wavefronts, a, gain: float, stream=None):
+    """POLC, SAFR and the integrator in one call; a is updated in place."""
+    _check(load().safr_loop_step(plan, _ptr(wavefronts), _ptr(a), float(gain), _stream(stream)), "safr_loop_step")
 
 
 def _ptr_array(xs):
