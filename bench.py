@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "passes"])
-    ap.add_argument("--no-workloads", action="store_true", help="skip the 32-grid, 512-grid, batched, learned-filter and loop-step workloads")
+    ap.add_argument("--no-workloads", action="store_true", help="skip the secondary workloads (32-grid, 512-grid, batched, learned filter, loop step, refresh)")
     return ap.parse_args()
 
 
@@ -361,6 +361,62 @@ def measure_loop(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm):
     return "loop-step-morfeo-256", out
 
 
+def measure_refresh(safr, synth, torch, dev, stream, steps):
+    """Soft real-time refresh of B on the MORFEO-like plan: safr_refresh with a
+    new alpha, and with a rotated asterism and a new Cn2 profile (tables copied,
+    Algorithm 2 rerun in place), timed with CUDA events on the stream; the
+    plan file round trip timed on the host."""
+    import tempfile
+    import time
+    g = synth.config(2)
+    plan = safr.Plan(g, device=dev.index)
+    rng = np.random.default_rng(12)
+
+    def timed(fn):
+        s0 = torch.cuda.Event(enable_timing=True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        fn()
+        e0.record(stream)
+        e0.synchronize()
+        return s0.elapsed_time(e0)
+
+    def new_asterism():
+        rot = rng.uniform(-0.05, 0.05)
+        dx, dy = np.asarray(g["dir_x"]), np.asarray(g["dir_y"])
+        return dict(cn2=np.asarray(g["cn2"]) * rng.uniform(0.8, 1.2, len(g["h"])),
+                    dir_x=np.cos(rot) * dx - np.sin(rot) * dy, dir_y=np.sin(rot) * dx + np.cos(rot) * dy)
+
+    for _ in range(3):
+        timed(lambda: safr.safr_refresh(plan.handle, alpha=g["alpha"], stream=stream))
+    t_alpha = sorted(timed(lambda: safr.safr_refresh(plan.handle, alpha=g["alpha"] * rng.uniform(0.5, 2), stream=stream))
+                     for _ in range(steps))
+    t_geo = sorted(timed(lambda: safr.safr_refresh(plan.handle, stream=stream, **new_asterism()))
+                   for _ in range(steps))
+    t_pre = sorted(timed(lambda: safr.safr_precompute(plan.handle, stream)) for _ in range(steps))
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "morfeo.safr")
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        safr.safr_plan_save(plan.handle, path)
+        t_save = time.perf_counter() - t0
+        size = os.path.getsize(path)
+        t0 = time.perf_counter()
+        q = safr.Plan.load(path, dev.index)
+        torch.cuda.synchronize(dev)
+        t_load = time.perf_counter() - t0
+        same = bool(np.array_equal(safr.safr_copy_B(q.handle, 0), safr.safr_copy_B(plan.handle, 0)))
+        q.close()
+    plan.close()
+    med = lambda v: float(v[len(v) // 2])  # noqa: E731
+    return "refresh-morfeo-256", {
+        "refresh_alpha_ms": {"p50": med(t_alpha), "max": float(t_alpha[-1])},
+        "refresh_asterism_and_profile_ms": {"p50": med(t_geo), "max": float(t_geo[-1])},
+        "precompute_only_ms": {"p50": med(t_pre)},
+        "plan_file": {"bytes": size, "save_ms": t_save * 1e3, "load_ms": t_load * 1e3, "B_identical": same},
+        "steps": steps}
+
+
 def measure_learned(safr, synth, torch, dev, stream, steps, warmup, flush_l2):
     """The learned spectral filter on the 32-grid geometry with 35 layers: GPU
     training on 100k forward-model frames (2 epochs), the held-out comparison
@@ -585,6 +641,8 @@ def run_safr(args):
         name, res = measure_learned(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2)
         workloads[name] = res
         name, res = measure_loop(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2, hbm_pk)
+        workloads[name] = res
+        name, res = measure_refresh(safr, synth, torch, dev, stream, 10)
         workloads[name] = res
 
     if rank == 0:

@@ -62,7 +62,8 @@ typedef enum {
     SAFR_ERR_OOM = 5,              /* cudaMalloc failed in safr_plan_create         */
     SAFR_ERR_CUDA = 6,             /* a CUDA runtime call failed (no device, launch) */
     SAFR_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up            */
-    SAFR_ERR_DEVICE = 8            /* a device-side check failed (see safr_get_status) */
+    SAFR_ERR_DEVICE = 8,           /* a device-side check failed (see safr_get_status) */
+    SAFR_ERR_IO = 9                /* a plan file could not be written or read, or is not a valid plan file */
 } safr_status;
 
 enum { SAFR_NGS = 0, SAFR_LGS = 1 };                           /* guide-star kind          */
@@ -465,6 +466,49 @@ safr_status safr_polc(safr_plan_t plan, const void *d_wavefronts, const void *d_
 safr_status safr_integrate(safr_plan_t plan, const void *d_layers, void *d_a, double gain, cudaStream_t stream);
 safr_status safr_loop_step(safr_plan_t plan, const void *d_wavefronts, void *d_a, double gain,
                            cudaStream_t stream);
+
+/*
+ * Soft real-time refresh (Algorithm 2; Section 3.4: B is recomputed whenever
+ * parameters at the telescope or in the atmosphere change, e.g. guide-star
+ * positions or the turbulence profile).  safr_refresh sets new layer weights
+ * (cn2 [L], normalised to sum 1 as at creation), new star directions
+ * (dir_x, dir_y [G], both or neither; the kinds of the stars are kept) and
+ * new regularisation parameters (alpha, alpha_tt; <= 0 keeps the current
+ * value).  NULL arrays keep the current values.  Layer heights, grid, pupil and
+ * star kinds cannot change (create a new plan).  The derived tables are
+ * copied into the plan's existing buffers and B is recomputed in place on
+ * `stream`: no allocation, and frames issued later on the same stream use the
+ * new B.  A learned filter's B is replaced by plain SAFR's (train or apply
+ * it again).  Argument errors are returned before anything changes.
+ */
+typedef struct {
+    const double *cn2;   /* [L] or NULL */
+    const double *dir_x; /* [G] or NULL */
+    const double *dir_y; /* [G] or NULL */
+    double alpha;        /* > 0 to change */
+    double alpha_tt;     /* > 0 to change */
+} safr_update;
+safr_status safr_refresh(safr_plan_t plan, const safr_update *update, cudaStream_t stream);
+
+/*
+ * Plan files.  safr_plan_save writes the plan's geometry and its B (as
+ * stored on the device, so a learned filter's B is kept) to `path`;
+ * synchronises the plan's device.  safr_plan_load reads such a file, creates
+ * the plan on `cuda_device` and uploads B without recomputing it; the new
+ * plan is precomputed.  Format (little-endian, packed):
+ *   char[8] "SAFRPLN1", u32 version = 1,
+ *   i32 M, P, L, G, precision, output_grid, remove_tt, learned (1: B is a learned filter's),
+ *   f64 pitch_m, diameter_m, obstruction, h_lgs_m, alpha, alpha_tt, beta,
+ *   f64 h_m[L], cn2[L], dir_x[G], dir_y[G], i32 kind[G],
+ *   u64 FNV-1a-64 of every byte above (the geometry hash),
+ *   u64 n, n bytes of B ([M/2][sum_groups L G_group][M] complex in the plan's
+ *   B precision, j in the frame kernels' order), u64 FNV-1a-64 of those n bytes.
+ * A file that cannot be read or written, a wrong magic, version, size or
+ * hash returns SAFR_ERR_IO; the file is checked before any device work.  A
+ * geometry that safr_plan_create rejects returns its status.
+ */
+safr_status safr_plan_save(safr_plan_t plan, const char *path);
+safr_status safr_plan_load(const char *path, int cuda_device, safr_plan_t *out);
 
 /* Free every device and host resource of the plan (synchronises its device). */
 safr_status safr_destroy(safr_plan_t plan);

@@ -18,6 +18,10 @@
  *   - hard real-time apply .......................... Algorithm 1
  *   - split tomography (LGS + TTS, results added) ... Section 3.3, Algorithm 3
  *   - removeTT (planar component of LGS wavefronts) . Section 3.3, Algorithm 3
+ *   - learned filter phi/sigma (MLP factor) ......... Section 3.1 (general filter g)
+ *   - Philox4x32-10 and the training frames ......... Salmon et al. (SC 2011); Section 2
+ *   - POLC, psi + A(a) with bilinear layers ......... Algorithm 3 line 2, Eq. (defAperonly)
+ *   - integrator ..................................... Algorithm 3 line 5
  *
  * Readings where the paper is silent or assumes odd M (all even-M grids):
  *   - Nyquist: the symmetric truncation keeps |n| <= M/2-1, so B is zero on the

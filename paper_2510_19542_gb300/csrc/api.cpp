@@ -174,6 +174,17 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     p->T = g->M * g->pitch_m / 2.0;
     p->beta = g->beta;
     p->h.assign(g->h_m, g->h_m + g->L);
+    // the geometry as given (plan files, refresh)
+    p->geo = *g;
+    p->geo_cn2.assign(g->cn2, g->cn2 + g->L);
+    p->geo_dir_x.assign(g->dir_x, g->dir_x + g->G);
+    p->geo_dir_y.assign(g->dir_y, g->dir_y + g->G);
+    p->geo_kind.assign(g->kind, g->kind + g->G);
+    p->geo.h_m = p->h.data();
+    p->geo.cn2 = p->geo_cn2.data();
+    p->geo.dir_x = p->geo_dir_x.data();
+    p->geo.dir_y = p->geo_dir_y.data();
+    p->geo.kind = p->geo_kind.data();
     double sum = 0;
     for (int l = 0; l < g->L; ++l) sum += g->cn2[l];
     p->gamma.resize(g->L);
@@ -210,17 +221,8 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
         gr.b_row0 = row0;
         row0 += g->L * cnt;
         gr.resample = gr.kind == SAFR_LGS && p->output_metric;
-        // containment c_l Omega_A + alpha_g h_l in c_l Omega_T (Section 2), per axis
-        const double ra = 0.5 * g->P * g->pitch_m;
-        for (int t = 0; t < cnt; ++t)
-            for (int l = 0; l < g->L; ++l) {
-                const int s = gr.stars[t];
-                const double c = gr.c[l];
-                if (c * ra + std::fabs(g->dir_x[s] * g->h_m[l]) > c * p->T ||
-                    c * ra + std::fabs(g->dir_y[s] * g->h_m[l]) > c * p->T)
-                    p->warnings |= SAFR_WARN_CONTAINMENT;
-            }
     }
+    p->warnings |= safr::containment_warnings(p);  // Section 2 containment, per axis
     p->sumLG = row0;
 
     // removeTT: the tip b and tilt c of the least-squares plane a + b x + c y
@@ -385,15 +387,7 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     SAFR_TRY(cudaMemset(p->d_bar, 0, 2 * sizeof(unsigned long long)));
 
     // precompute inputs: per group sx, sy [G][L], sw [L], tau [L]
-    std::vector<double> pre;
-    for (int gi = 0; gi < p->ngroups; ++gi) {
-        const safr::Group &gr = p->grp[gi];
-        pre.insert(pre.end(), gr.sx.begin(), gr.sx.end());
-        pre.insert(pre.end(), gr.sy.begin(), gr.sy.end());
-        for (int l = 0; l < L; ++l) pre.push_back(std::sqrt(p->gamma[l]) / gr.c[l]);
-        for (int l = 0; l < L; ++l) pre.push_back(kPi * kPi / ((gr.c[l] * p->T) * (gr.c[l] * p->T)));
-    }
-    SAFR_TRY(upload(&p->d_pre, pre));
+    SAFR_TRY(upload(&p->d_pre, safr::pre_inputs(p)));
 
     SAFR_TRY(cudaMalloc((void **)&p->d_status, sizeof(int)));
     SAFR_TRY(cudaMemset(p->d_status, 0, sizeof(int)));
@@ -697,6 +691,7 @@ const char *safr_status_string(safr_status s)
     case SAFR_ERR_CUDA: return "SAFR_ERR_CUDA: CUDA runtime error";
     case SAFR_ERR_TIMEOUT: return "SAFR_ERR_TIMEOUT: a bounded device-side wait gave up";
     case SAFR_ERR_DEVICE: return "SAFR_ERR_DEVICE: a device-side check failed";
+    case SAFR_ERR_IO: return "SAFR_ERR_IO: plan file not written or read, or not a valid plan file";
     }
     return "unknown safr_status";
 }

@@ -736,6 +736,13 @@ struct FilterState {
     bool basis_ready = false, training = false;
 };
 
+void filter_invalidate(safr_plan_s *pl)
+{
+    FilterState *fs = (FilterState *)pl->filter;
+    if (fs) fs->basis_ready = false;
+    pl->filter_learned = 0;
+}
+
 void filter_free(safr_plan_s *pl)
 {
     FilterState *fs = (FilterState *)pl->filter;

@@ -84,6 +84,9 @@ struct safr_plan_s {
     double delta = 0, T = 0, beta = 0;
     double diameter = 0, obstruction = 0;  // pupil annulus (diameter <= 0: the whole P x P square)
     std::vector<double> h, gamma;
+    safr_geometry geo{};  // the geometry as given; its arrays point into h and the geo_* vectors
+    std::vector<double> geo_cn2, geo_dir_x, geo_dir_y;
+    std::vector<int> geo_kind;
     int ngroups = 0;
     safr::Group grp[2];
     int sumLG = 0;
@@ -156,7 +159,10 @@ cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scal
                          cudaStream_t stream);
 void frame2_twiddles(int M, std::vector<double> &re, std::vector<double> &im);
 void filter_free(safr_plan_s *plan);
+void filter_invalidate(safr_plan_s *plan);  // the SVD basis is stale (the geometry changed)
 void polc_table(const safr_plan_s *plan, std::vector<unsigned char> &bytes);
+std::vector<double> pre_inputs(const safr_plan_s *plan);    // refresh.cpp
+int containment_warnings(const safr_plan_s *plan);          // refresh.cpp
 inline bool use_fused(const safr_plan_s *plan)
 {
     return plan->fused_ok && plan->path != SAFR_PATH_PASSES;

@@ -24,6 +24,7 @@ SAFR_ERR_OOM = 5
 SAFR_ERR_CUDA = 6
 SAFR_ERR_TIMEOUT = 7
 SAFR_ERR_DEVICE = 8
+SAFR_ERR_IO = 9
 
 SAFR_NGS, SAFR_LGS = 0, 1
 SAFR_FP32, SAFR_FP16_STORAGE, SAFR_FP64 = 0, 1, 2
@@ -38,7 +39,8 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_destroy", "safr_status_string", "safr_reconstruct_noalloc", "safr_autotune",
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
-            "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step"]
+            "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
+            "safr_plan_save", "safr_plan_load"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -64,6 +66,11 @@ class safr_plan_info(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("in_bytes", C.c_size_t), ("out_bytes", C.c_size_t),
                 ("warnings", C.c_int), ("precomputed", C.c_int), ("path", C.c_int), ("tile_rows", C.c_int),
                 ("autotuned", C.c_int)]
+
+
+class safr_update(C.Structure):
+    _fields_ = [("cn2", C.POINTER(C.c_double)), ("dir_x", C.POINTER(C.c_double)), ("dir_y", C.POINTER(C.c_double)),
+                ("alpha", C.c_double), ("alpha_tt", C.c_double)]
 
 
 class safr_filter_config(C.Structure):
@@ -123,6 +130,9 @@ def load(build_if_missing: bool = True):
                                       C.POINTER(safr_filter_result), vp]
     lib.safr_filter_apply.argtypes = [vp, C.POINTER(C.c_float), C.c_double, vp]
     lib.safr_filter_reset.argtypes = [vp, vp]
+    lib.safr_refresh.argtypes = [vp, C.POINTER(safr_update), vp]
+    lib.safr_plan_save.argtypes = [vp, C.c_char_p]
+    lib.safr_plan_load.argtypes = [C.c_char_p, C.c_int, C.POINTER(vp)]
     lib.safr_polc.argtypes = [vp, vp, vp, vp, vp]
     lib.safr_integrate.argtypes = [vp, vp, vp, C.c_double, vp]
     lib.safr_loop_step.argtypes = [vp, vp, vp, C.c_double, vp]
@@ -330,6 +340,32 @@ def safr_loop_step(plan: int, wavefronts, a, gain: float, stream=None):
     _check(load().safr_loop_step(plan, _ptr(wavefronts), _ptr(a), float(gain), _stream(stream)), "safr_loop_step")
 
 
+def safr_refresh(plan: int, cn2=None, dir_x=None, dir_y=None, alpha: float = 0.0, alpha_tt: float = 0.0,
+                 stream=None):
+    """New layer weights, star directions or alphas; B recomputed in place on the stream."""
+    keep = []
+
+    def arr(x):
+        if x is None:
+            return None
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        keep.append(a)
+        return a.ctypes.data_as(C.POINTER(C.c_double))
+
+    u = safr_update(arr(cn2), arr(dir_x), arr(dir_y), float(alpha), float(alpha_tt))
+    _check(load().safr_refresh(plan, C.byref(u), _stream(stream)), "safr_refresh")
+
+
+def safr_plan_save(plan: int, path: str):
+    _check(load().safr_plan_save(plan, os.fsencode(path)), "safr_plan_save")
+
+
+def safr_plan_load(path: str, cuda_device: int = 0) -> int:
+    out = C.c_void_p()
+    _check(load().safr_plan_load(os.fsencode(path), int(cuda_device), C.byref(out)), "safr_plan_load")
+    return out.value
+
+
 def _ptr_array(xs):
     if xs is None:
         return None
@@ -386,6 +422,19 @@ class Plan:
         if precompute:
             safr_precompute(self.handle, stream)
             self.info["precomputed"] = 1
+
+    @classmethod
+    def load(cls, path: str, device: int = 0):
+        """A plan from a file written by safr_plan_save (B uploaded, not recomputed)."""
+        with open(path, "rb") as f:
+            head = f.read(12 + 8 * 4)
+        precision = int(np.frombuffer(head[12:], dtype="<i4")[4])
+        self = cls.__new__(cls)
+        self.handle = safr_plan_load(path, device)
+        self.device = device
+        self.info = safr_get_plan_info(self.handle)
+        self.geom = {"precision": {SAFR_FP32: "fp32", SAFR_FP16_STORAGE: "fp16", SAFR_FP64: "fp64"}[precision]}
+        return self
 
     def close(self):
         if getattr(self, "handle", None):

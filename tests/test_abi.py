@@ -38,7 +38,7 @@ def test_binding_names_match_the_abi():
 
 def test_status_strings(lib):
     from paper_2510_19542_gb300 import safr
-    for s in range(9):
+    for s in range(10):
         assert safr.safr_status_string(s).startswith("SAFR_")
     assert "unknown" in safr.safr_status_string(99)
 
