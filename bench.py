@@ -53,12 +53,17 @@ def parse():
     return ap.parse_args()
 
 
+# the sources the persistent frame kernel is compiled from (its counters go stale when one changes)
+FRAME_KERNEL_SOURCES = ("common.cuh", "frame.cu", "frame_dispatch.cuh", "frame_f16.cu", "frame_f32.cu",
+                        "frame_f64.cu", "frame_impl.cuh", "freqorder.h", "plan.h", "warpfft.cuh")
+
+
 def csrc_sha256() -> str:
-    """sha256 over the library sources (file name and bytes, sorted by name)."""
+    """sha256 over the frame kernel's sources (file name and bytes, sorted by name)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2510_19542_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
+    for name in sorted(FRAME_KERNEL_SOURCES):
         with open(os.path.join(d, name), "rb") as f:
             h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()
