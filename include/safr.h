@@ -230,6 +230,14 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
  */
 safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out);
 
+/*
+ * The raw timestamps of the last traced persistent-kernel frame: us[b * 23 + i]
+ * = mark i of CTA b in microseconds from the earliest CTA start (0 where the
+ * CTA never reached the mark), for the n_cta CTAs of the launch; writes at
+ * most n values, *n_cta = the grid size.  Errors as safr_trace_phases.
+ */
+safr_status safr_trace_stamps(safr_plan_t plan, double *us, int n, int *n_cta);
+
 /* Number of kernel launches one safr_reconstruct makes for this plan. */
 int safr_launches_per_frame(safr_plan_t plan);
 

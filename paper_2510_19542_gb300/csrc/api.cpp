@@ -644,6 +644,26 @@ safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out)
     return SAFR_OK;
 }
 
+safr_status safr_trace_stamps(safr_plan_t plan, double *us, int n, int *n_cta)
+{
+    if (!plan || (!us && n > 0)) return SAFR_ERR_INVALID_ARG;
+    if (n_cta) *n_cta = 0;
+    if (!plan->traced || !safr::use_fused(plan) || !plan->d_stamps) return SAFR_ERR_INVALID_ARG;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return SAFR_ERR_CUDA;
+    if (cudaEventSynchronize(plan->ev[1]) != cudaSuccess) return SAFR_ERR_CUDA;
+    const int K = SAFR_TRACE_MARKS;
+    std::vector<unsigned long long> st((size_t)plan->f2_grid * K);
+    if (cudaMemcpy(st.data(), plan->d_stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+        return SAFR_ERR_CUDA;
+    unsigned long long t0 = ~0ull;
+    for (int b = 0; b < plan->f2_grid; ++b) t0 = std::min(t0, st[(size_t)b * K]);
+    for (size_t i = 0; i < st.size() && (long)i < n; ++i) us[i] = st[i] > t0 ? 1e-3 * (double)(st[i] - t0) : 0.0;
+    if (n_cta) *n_cta = plan->f2_grid;
+    return SAFR_OK;
+}
+
 safr_status safr_set_path(safr_plan_t plan, int path)
 {
     if (!plan || path < SAFR_PATH_AUTO || path > SAFR_PATH_PASSES) return SAFR_ERR_INVALID_ARG;

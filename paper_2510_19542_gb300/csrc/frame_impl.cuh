@@ -107,6 +107,24 @@ __device__ __forceinline__ unsigned long long gtimer()
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// a complex value from shared memory at byte address a (shared window)
+template <typename C>
+__device__ __forceinline__ C lds_c(unsigned a);
+template <>
+__device__ __forceinline__ float2 lds_c<float2>(unsigned a)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+template <>
+__device__ __forceinline__ double2 lds_c<double2>(unsigned a)
+{
+    double2 v;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count)
 {
     asm volatile("mbarrier.init.shared.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
@@ -345,22 +363,52 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             const R sc = fp.in_scales ? (R)fp.in_scales[g] : R(1);
             const bool tt = act && fp.any_tt && s_star_tt[g];
             const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
-            // z[q] = psi[a0][q - o] + i psi[a0 + 1][q - o]: lane t holds q = t + LW r
+            // z[q] = psi[a0][q - o] + i psi[a0 + 1][q - o]: lane t holds q = t + LW r.
+            // Loads are issued in batches, from clamped in-range addresses, before any
+            // is used (the two rows, then each row's tip/tilt weights); values out of
+            // range are selected away.
             C v[RR];
             R s0b = 0, s0c = 0, s1b = 0, s1c = 0;
+            const int a1 = has1 ? a0 + 1 : a0;
+            {
+                R x0[RR], x1[RR];
 #pragma unroll
-            for (int r = 0; r < RR; ++r) {
-                const int qq = t + LW * r - o;
-                const bool in = act && qq >= 0 && qq < P;
-                const R x0 = in ? load_in<R>(psi + (size_t)a0 * P + qq) : R(0);
-                const R x1 = in && has1 ? load_in<R>(psi + (size_t)(a0 + 1) * P + qq) : R(0);
-                v[r] = C{x0 * sc, x1 * sc};
-                if (tt && in) {
-                    s0b += wb[a0 * P + qq] * v[r].x;
-                    s0c += wc[a0 * P + qq] * v[r].x;
-                    if (has1) {
-                        s1b += wb[(a0 + 1) * P + qq] * v[r].y;
-                        s1c += wc[(a0 + 1) * P + qq] * v[r].y;
+                for (int r = 0; r < RR; ++r) {
+                    const int qc = min(max(t + LW * r - o, 0), P - 1);
+                    x0[r] = load_in<R>(psi + (size_t)a0 * P + qc);
+                    x1[r] = load_in<R>(psi + (size_t)a1 * P + qc);
+                }
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int qq = t + LW * r - o;
+                    const bool in = act && qq >= 0 && qq < P;
+                    v[r] = C{in ? x0[r] * sc : R(0), in && has1 ? x1[r] * sc : R(0)};
+                }
+            }
+            if (tt) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int a = h ? a1 : a0;
+                    R wbr[RR], wcr[RR];
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const int qc = min(max(t + LW * r - o, 0), P - 1);
+                        wbr[r] = wb[a * P + qc];
+                        wcr[r] = wc[a * P + qc];
+                    }
+                    R sb = 0, scc = 0;
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const R x = h ? v[r].y : v[r].x;
+                        sb += wbr[r] * x;
+                        scc += wcr[r] * x;
+                    }
+                    if (h) {
+                        s1b = sb;
+                        s1c = scc;
+                    } else {
+                        s0b = sb;
+                        s0c = scc;
                     }
                 }
             }
@@ -438,9 +486,11 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 const C *src = fp.w1 + ((size_t)ss * Mh + k) * P;
                 C v[RR];
 #pragma unroll
-                for (int r = 0; r < RR; ++r) {
+                for (int r = 0; r < RR; ++r) v[r] = __ldcg(src + min(max(t + LW * r - o, 0), P - 1));
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {  // loads first (clamped addresses), then the zero extension
                     const int pp = t + LW * r - o;
-                    v[r] = act && pp >= 0 && pp < P ? __ldcg(src + pp) : C{0, 0};
+                    if (!(act && pp >= 0 && pp < P)) v[r] = C{0, 0};
                 }
                 const bool tt = fp.any_tt && act && s_star_tt[ss];
                 if (first_col && fp.any_tt) {
@@ -522,19 +572,28 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 for (int q = 0; q < LPS; ++q)
 #pragma unroll
                     for (int r = 0; r < RR; ++r) v[q][r] = C{0, 0};
-                for (int gg = 0; gg < gG; ++gg) {
-                    const C *Dg = Dp + (size_t)s_grp[gi].star[gg] * M;
+                // B from shared memory (staged) by ld.shared, else from global memory
+                auto apply = [&](auto loadB) {
+                    for (int gg = 0; gg < gG; ++gg) {
+                        const C *Dg = Dp + (size_t)s_grp[gi].star[gg] * M;
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        const int pos = r * LW + t;
-                        const C dv = Dg[pos];
+                        for (int r = 0; r < RR; ++r) {
+                            const int pos = r * LW + t;
+                            const C dv = Dg[pos];
 #pragma unroll
-                        for (int q = 0; q < LPS; ++q) {
-                            const C bv = Bl[((size_t)(gg + (q < nl ? q : 0) * gG) << LOGM) + pos];
-                            v[q][r].x += bv.x * dv.x - bv.y * dv.y;
-                            v[q][r].y += bv.x * dv.y + bv.y * dv.x;
+                            for (int q = 0; q < LPS; ++q) {
+                                const C bv = loadB(((size_t)(gg + (q < nl ? q : 0) * gG) << LOGM) + pos);
+                                v[q][r].x += bv.x * dv.x - bv.y * dv.y;
+                                v[q][r].y += bv.x * dv.y + bv.y * dv.x;
+                            }
                         }
                     }
+                };
+                if (fp.stage_b) {
+                    const unsigned bl = smem_u32(Bl);
+                    apply([&](size_t i) { return lds_c<C>(bl + (unsigned)(i * sizeof(C))); });
+                } else {
+                    apply([&](size_t i) { return __ldcg(Bl + i); });
                 }
                 SAFR_MARK(11, k == b && u0 == 0);
                 if (fp.energy) {  // Parseval partial sums of |b_l(j, k)|^2 over j
@@ -649,33 +708,34 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             for (int u0 = 0; u0 < ntot; u0 += UNITS) {
                 const int task = u0 + unit;
                 const bool act = task < ntot;
-                const bool g1 = task >= npair0;
-                const int i = g1 ? task - npair0 : task;
+                const int tk = act ? task : 0;  // an idle slot reads row pair 0 of group 0 (always staged)
+                const bool g1 = tk >= npair0;
+                const int i = g1 ? tk - npair0 : tk;
                 const C *sg = g1 ? stg1 : stg0;
                 const int st = g1 ? st1 : st0;
                 const bool hasb = 2 * i + 1 < (g1 ? nsrc1 : nsrc0);
-                C v[RR];
+                // frequency k < M/2 reads stored column k; k > M/2 reads column M - k (conjugate
+                // symmetry); every lane loads from a valid address first, then selects
+                C v[RR], x1[RR], x2[RR];
+                const int ib = hasb ? 2 * i + 1 : 2 * i;
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     const int k = r + RR * bt;
-                    C z = C{0, 0};
-                    if (act && k < Mh) {
-                        const C *row = sg + k * st + (((k / RR) >> 1) & 15);
-                        C x1 = row[2 * i];
-                        C x2 = hasb ? row[2 * i + 1] : C{0, 0};
-                        if (k == 0) {
-                            x1.y = 0;
-                            x2.y = 0;
-                        }
-                        z = C{x1.x - x2.y, x1.y + x2.x};
-                    } else if (act && k > Mh) {
-                        const int kk = M - k;
-                        const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
-                        const C x1 = row[2 * i];
-                        const C x2 = hasb ? row[2 * i + 1] : C{0, 0};
-                        z = C{x1.x + x2.y, x2.x - x1.y};
+                    const int kk = k < Mh ? k : (k > Mh ? M - k : 0);
+                    const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
+                    x1[r] = row[2 * i];
+                    x2[r] = row[ib];
+                }
+#pragma unroll
+                for (int r = 0; r < RR; ++r) {
+                    const int k = r + RR * bt;
+                    C a = x1[r], c = hasb ? x2[r] : C{0, 0};
+                    if (k == 0) {
+                        a.y = 0;
+                        c.y = 0;
                     }
-                    v[r] = z;
+                    const C lo = C{a.x - c.y, a.y + c.x}, hi = C{a.x + c.y, c.x - a.y};
+                    v[r] = !act || k == Mh ? C{0, 0} : (k < Mh ? lo : hi);
                 }
                 wfft_inv<M>(v, tw, t);
                 if (act)

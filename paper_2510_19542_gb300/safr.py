@@ -40,7 +40,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
             "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
-            "safr_plan_save", "safr_plan_load"]
+            "safr_plan_save", "safr_plan_load", "safr_trace_stamps"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
     lib.safr_trace_read.argtypes = [vp, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]
     lib.safr_launches_per_frame.argtypes = [vp]
     lib.safr_trace_phases.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
+    lib.safr_trace_stamps.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     lib.safr_set_path.argtypes = [vp, C.c_int]
     lib.safr_get_path.argtypes = [vp]
     lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
@@ -268,6 +269,16 @@ def safr_trace_phases(plan: int):
             "p2_star_fft", "p2_synced", "p2_B_landed", "p2_apply", "p2_inv_fft", "p2_stored", "p2_done",
             "bar2_arrive", "bar2_out", "p3_tables", "p3_staged", "p3_fft", "p3_synced", "p3_first_stored", "p3_done"]
     return dict(zip(keys, [us[i] for i in range(n.value)]))
+
+
+def safr_trace_stamps(plan: int) -> np.ndarray:
+    """Per-CTA phase marks (us) of the last traced persistent-kernel frame, [n_cta][23]."""
+    cap = 4096 * 23
+    us = np.zeros(cap, np.float64)
+    n = C.c_int(0)
+    _check(load().safr_trace_stamps(plan, us.ctypes.data_as(C.POINTER(C.c_double)), cap, C.byref(n)),
+           "safr_trace_stamps")
+    return us[:n.value * 23].reshape(n.value, 23)
 
 
 def safr_launches_per_frame(plan: int) -> int:
