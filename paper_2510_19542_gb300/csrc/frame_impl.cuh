@@ -357,6 +357,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         for (int base = lo; base < hi; base += UNITS) {
             const int i = base + unit;
             const bool act = i < hi;
+            if (!__any_sync(0xffffffffu, act)) continue;  // a warp with no transform in this round stays idle
             const int item = act ? i : lo, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
             const bool has1 = a0 + 1 < P;
             const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
@@ -482,6 +483,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             for (int s0 = 0; s0 < G; s0 += UNITS) {
                 const int s = s0 + unit;
                 const bool act = s < G;
+                if (!__any_sync(0xffffffffu, act)) continue;
                 const int ss = act ? s : 0;
                 const C *src = fp.w1 + ((size_t)ss * Mh + k) * P;
                 C v[RR];
@@ -563,6 +565,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             for (int u0 = 0; u0 < nslot; u0 += UNITS) {
                 const int pt = u0 + unit;
                 const bool act = pt < nslot;
+                if (!__any_sync(0xffffffffu, act)) continue;
                 const int ptk = act ? pt : 0, gi = ptk >= per ? 1 : 0, l0 = LPS * (ptk - gi * per);
                 const int nl = min(LPS, L - l0);
                 const int gG = s_grp[gi].G;
@@ -708,6 +711,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             for (int u0 = 0; u0 < ntot; u0 += UNITS) {
                 const int task = u0 + unit;
                 const bool act = task < ntot;
+                if (!__any_sync(0xffffffffu, act)) continue;
                 const int tk = act ? task : 0;  // an idle slot reads row pair 0 of group 0 (always staged)
                 const bool g1 = tk >= npair0;
                 const int i = g1 ? tk - npair0 : tk;
