@@ -252,11 +252,12 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     const int t = lane & (LW - 1);                             // lane within the transform
     const int unit = warp * S::TPW + (lane >> LB);             // transform slot of this lane
     const int bt = LB > 0 ? (int)(__brev((unsigned)t) >> (32 - LB)) : 0;  // brev(t)
-    if (warp == 0) {
+    // parameter copies by warps 2 and 3 (warp 0 issues the table copies first)
+    if (warp == 2) {
 #pragma unroll
         for (int i = 0; i < SAFR_MAX_G; ++i)
             if (lane == (i & 31)) s_star_tt[i] = fp.star_tt[i];
-    } else if (warp == 1) {
+    } else if (warp == 3) {
 #pragma unroll
         for (int gi = 0; gi < 2; ++gi) {
             if (lane == 0) {
@@ -297,14 +298,12 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             tma_load_1d((unsigned char *)Bs + off, (const unsigned char *)src + off, min(32768u, colB_bytes - off),
                         &mbar);
     };
-    __shared__ C s_w32[32];
-    wtw_fill_w32(s_w32);
     WTw<M, C> tw;
     // tables, one bulk copy each into shared memory of their own, completing on
     // mbar_t: the warp-FFT twiddles, this CTA's first phase-2 column of the
     // removeTT spectra and its first phase-3 item's resample tables
     __shared__ __align__(8) uint64_t mbar_t;
-    C *twq_s = (C *)(smem + fp.off_tw);     // [M]
+    C *twq_s = (C *)(smem + fp.off_tw);     // [M + LW]
     int *ti0 = (int *)(smem + fp.off_rs);  // [M]
     R *tfw = (R *)(ti0 + M);               // [M]
     const bool xy_pre = fp.any_tt && b < Mh;
@@ -316,8 +315,9 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         const unsigned cb = (unsigned)(M * sizeof(C)), ib = (unsigned)(M * 4), wb = (unsigned)(M * sizeof(R));
-        mbar_expect_tx(&mbar_t, cb + (xy_pre ? 2 * cb : 0u) + (rs_pre ? ib + wb : 0u));
-        tma_load_1d(twq_s, fp.twq, cb, &mbar_t);
+        const unsigned tb = (unsigned)((M + LW) * sizeof(C));
+        mbar_expect_tx(&mbar_t, tb + (xy_pre ? 2 * cb : 0u) + (rs_pre ? ib + wb : 0u));
+        tma_load_1d(twq_s, fp.twq, tb, &mbar_t);
         if (xy_pre) {
             tma_load_1d(xys, fp.xy_hat + ((size_t)b << LOGM), cb, &mbar_t);
             tma_load_1d(xys + M, fp.xy_hat + ((size_t)(Mh + b) << LOGM), cb, &mbar_t);
@@ -332,7 +332,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     // on a timeout here: the status word records it and the barriers stay balanced)
     auto tables = [&]() {
         mbar_wait_bounded(&mbar_t, tph, fp.timeout_ns, fp.status);
-        tw.load(twq_s, s_w32, t);
+        tw.load(twq_s, t);
     };
     {   // later columns of this CTA (or every column when B is not staged): into L2
         const int k0 = fp.stage_b ? b + nb : b;
@@ -342,7 +342,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 prefetch_l2(base + off, min(4096u, colB_bytes - off));
         }
     }
-    __syncthreads();  // the W_32 table and the parameter copies
+    __syncthreads();  // the parameter copies
     SAFR_MARK(1, true);
 
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
@@ -855,8 +855,8 @@ struct Frame2Host {
         // phase 1 / 2: B column block, column spectra, removeTT stash
         bool any_rs = false;
         for (int gi = 0; gi < pl->ngroups; ++gi) any_rs |= pl->grp[gi].resample;
-        // resample tables (whole kernel), then the twiddle table (until the first transform)
-        const size_t rsb = (any_rs ? al((size_t)M * (4 + rs)) : 0) + al((size_t)M * cs);
+        // resample tables and the twiddle table [M + LW] (both read for the whole kernel)
+        const size_t rsb = (any_rs ? al((size_t)M * (4 + rs)) : 0) + al((size_t)(M + wfft_lanes(M)) * cs);
         const size_t colB = (size_t)pl->sumLG * M * cs;
         const size_t db = al((size_t)G * M * cs);
         const size_t xyb = pl->remove_tt ? al(2 * (size_t)M * cs) : 0;

@@ -17,9 +17,8 @@
 // No shared memory and no block barrier: every lane of the warp must call the
 // functions together (lanes of unused transforms compute on any values).
 // The R-point DFTs are recursive radix-2 decimation in time, fully unrolled,
-// with the exact constants cos(pi m / 16); the lane-stage twiddles W_LW^e are
-// the same constants; the W_M^(t k_r) twiddles come from a table built on the
-// host in FP64.
+// with the exact constants cos(pi m / 16); the lane-stage twiddles W_LW^e and
+// the W_M^(t k_r) twiddles come from a table built on the host in FP64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -110,55 +109,21 @@ struct WShape {
     static constexpr int LOG = ilog2c(M);
 };
 
-// exp(-2 pi i e / 32) for 0 <= e < 32, from the exact constants cos(pi m / 16).
-// Branches on e: fill a table with it once, do not call it per lane in a loop.
-template <typename C>
-__device__ __forceinline__ C w32(int e)
-{
-    using R = decltype(C{}.x);
-    auto cpi16 = [](int m) -> R {  // cos(pi m / 16), 0 <= m < 32
-        const int a = m & 15;
-        const int f = a <= 8 ? a : 16 - a;  // fold to [0, 8]
-        R v;
-        switch (f) {
-        case 0: v = (R)cos_pi16(0); break;
-        case 1: v = (R)cos_pi16(1); break;
-        case 2: v = (R)cos_pi16(2); break;
-        case 3: v = (R)cos_pi16(3); break;
-        case 4: v = (R)cos_pi16(4); break;
-        case 5: v = (R)cos_pi16(5); break;
-        case 6: v = (R)cos_pi16(6); break;
-        case 7: v = (R)cos_pi16(7); break;
-        default: v = (R)0; break;
-        }
-        // cos(pi m / 16) < 0 for m in (8, 24)
-        return (m > 8 && m < 24) ? -v : v;
-    };
-    return C{cpi16(e), -cpi16((e + 24) & 31)};  // sin(x) = cos(x - pi/2)
-}
-
-// Per-lane twiddles W_M^(t k_r) (table layout, host FP64: tab[k_r * LW + t]) and
-// the lane-stage twiddles W_32^e, e < 32 (a table in shared memory, filled by
-// wtw_fill_w32 before the first transform).
+// Per-lane twiddles W_M^(t k_r) and the lane-stage twiddles W_LW^e, e < LW, from one
+// table built on the host in FP64 and copied into shared memory (layout:
+// tab[k_r * LW + t], then tab[M + e]).
 template <int M, typename C>
 struct WTw {
     using S = WShape<M>;
     C tw[S::R];
-    const C *w32s;
-    __device__ __forceinline__ void load(const C *tab, const C *w32_table, int t)
+    const C *wlw;  // W_LW^e, e < LW
+    __device__ __forceinline__ void load(const C *tab, int t)
     {
 #pragma unroll
         for (int k = 0; k < S::R; ++k) tw[k] = tab[k * S::LW + t];
-        w32s = w32_table;
+        wlw = tab + M;
     }
 };
-
-// threads 0..31 of the block write W_32^e to table[e]
-template <typename C>
-__device__ __forceinline__ void wtw_fill_w32(C *table)
-{
-    if (threadIdx.x < 32) table[threadIdx.x] = w32<C>((int)threadIdx.x);
-}
 
 template <typename C>
 __device__ __forceinline__ C shfl_xor_c(C v, int m)
@@ -174,14 +139,14 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[WShape<M>::R], const WTw<M, C> &
     dft_reg<S::R, false>(v);
 #pragma unroll
     for (int k = 1; k < S::R; ++k) v[k] = c_mul(v[k], w.tw[k]);
-    // stage h: W_(2h)^(t mod h) = W_32^((t mod h) * 16 / h)
+    // stage h: W_(2h)^(t mod h) = W_LW^((t mod h) * LW / (2h))
 #pragma unroll 1
     for (int h = S::LW / 2; h > 0; h >>= 1) {
         // upper lane: v + p; lower lane: (p - v) W.  As (sg v + p) wp with sg = -1, wp = W on the
         // lower lane and sg = 1, wp = 1 on the upper one.
         using R = decltype(C{}.x);
         const bool low = (t & h) != 0;
-        const C ws = w.w32s[(t & (h - 1)) * (16 / h)];
+        const C ws = w.wlw[(t & (h - 1)) * (S::LW / (2 * h))];
         const C wp = low ? ws : C{R(1), R(0)};
         const R sg = low ? R(-1) : R(1);
 #pragma unroll
@@ -202,7 +167,7 @@ __device__ __forceinline__ void wfft_inv(C (&v)[WShape<M>::R], const WTw<M, C> &
         // lower lane: u = v conj(W), result p - u; upper lane: u = v, result u + p
         using R = decltype(C{}.x);
         const bool low = (t & h) != 0;
-        const C ws = w.w32s[(t & (h - 1)) * (16 / h)];
+        const C ws = w.wlw[(t & (h - 1)) * (S::LW / (2 * h))];
         const C wc = low ? C{ws.x, -ws.y} : C{R(1), R(0)};
         const R sg = low ? R(-1) : R(1);
 #pragma unroll
