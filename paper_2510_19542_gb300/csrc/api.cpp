@@ -45,7 +45,7 @@ void free_plan_memory(safr_plan_s *p)
     void *bufs[] = {p->d_B, p->d_w1, p->d_w2, p->d_energy, p->d_tw, p->d_rs_i0, p->d_rs_w, p->d_mask, p->d_tt_w,
                     p->d_xy_hat, p->d_pm, p->d_bar, p->d_stamps, p->d_twq,
                     p->d_pre, p->d_status, p->d_in_stage, p->d_out_stage, p->d_in_scales_stage,
-                    p->d_out_scales_stage, p->d_polc};
+                    p->d_out_scales_stage, p->d_polc, p->d_mask_bits};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (auto &e : p->ev)
@@ -257,6 +257,17 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
                 ttw[PP + i] = inv[2][0] + inv[2][1] * x + inv[2][2] * y;
             }
         for (int i = 0; i < g->G; ++i) p->star_tt[i] = g->kind[i] == SAFR_LGS;
+        // the same functionals in closed form for the persistent kernel: w_b = mask (n10 + n11 x + n12 y),
+        // w_c = mask (n20 + n21 x + n22 y), and the mask as one bit per pixel
+        for (int v = 0; v < 3; ++v) {
+            p->tt_n[v] = inv[1][v];
+            p->tt_n[3 + v] = inv[2][v];
+        }
+        const int words = (g->P + 31) / 32;
+        p->mask_bits.assign((size_t)g->P * words, 0u);
+        for (int a = 0; a < g->P; ++a)
+            for (int b = 0; b < g->P; ++b)
+                if (mask[(size_t)a * g->P + b]) p->mask_bits[(size_t)a * words + (b >> 5)] |= 1u << (b & 31);
     }
 
     // ---------------- device memory ----------------
@@ -314,6 +325,7 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
         SAFR_TRY(upload((float **)&p->d_rs_w, ff));
     }
     SAFR_TRY(upload(&p->d_mask, mask));
+    if (!p->mask_bits.empty()) SAFR_TRY(upload(&p->d_mask_bits, p->mask_bits));
     {  // sample points of the POLC operator (loop.cu)
         std::vector<unsigned char> tab;
         safr::polc_table(p, tab);

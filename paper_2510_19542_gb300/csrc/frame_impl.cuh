@@ -88,7 +88,11 @@ struct Frame2Params {
     const C *twq;              // [M + LW] warp-FFT twiddles (WTw layout)
     const int *rs_i0;          // [L][M]
     const R *rs_w;             // [L][M]
-    const R *tt_w;             // [2][P][P]
+    const R *tt_w;             // [2][P][P] (not read by this kernel)
+    R tt_n[6];                 // removeTT: w_b = mask (n0 + n1 x + n2 y), w_c = mask (n3 + n4 x + n5 y)
+    R tt_delta;                // pixel pitch for x, y
+    const unsigned *mask_bits; // [P][mask_words] pupil mask, one bit per pixel
+    int mask_words;
     const C *xy_hat;           // [2][M/2][M], j in the permuted order
     R *pm;                     // [G][P][2]
     unsigned long long *bar;   // [2] arrival count, grid barriers completed before the launch
@@ -363,21 +367,29 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
             const R sc = fp.in_scales ? (R)fp.in_scales[g] : R(1);
             const bool tt = act && fp.any_tt && s_star_tt[g];
-            const R *wb = fp.tt_w, *wc = fp.tt_w + (size_t)P * P;
             // z[q] = psi[a0][q - o] + i psi[a0 + 1][q - o]: lane t holds q = t + LW r.
-            // Loads are issued in batches, from clamped in-range addresses, before any
-            // is used (the two rows, then each row's tip/tilt weights); values out of
-            // range are selected away.
+            // All loads (the two rows and, for removeTT, their pupil-mask words) are issued
+            // from clamped in-range addresses before any is used; values out of range are
+            // selected away.  The tip/tilt shares of a row are
+            //   sum_q w_b[a][q] psi[a][q] = (n0 + n1 x_a) S0 + n2 S1,  S0 = sum_q m psi, S1 = sum_q m y_q psi
+            // (w_b = mask (n0 + n1 x + n2 y), likewise w_c with n3..n5).
             C v[RR];
             R s0b = 0, s0c = 0, s1b = 0, s1c = 0;
             const int a1 = has1 ? a0 + 1 : a0;
             {
                 R x0[RR], x1[RR];
+                unsigned m0[RR], m1[RR];
+                const unsigned *mb0 = fp.mask_bits + (size_t)a0 * fp.mask_words;
+                const unsigned *mb1 = fp.mask_bits + (size_t)a1 * fp.mask_words;
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     const int qc = min(max(t + LW * r - o, 0), P - 1);
                     x0[r] = load_in<R>(psi + (size_t)a0 * P + qc);
                     x1[r] = load_in<R>(psi + (size_t)a1 * P + qc);
+                    if (tt) {
+                        m0[r] = mb0[qc >> 5];
+                        m1[r] = mb1[qc >> 5];
+                    }
                 }
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
@@ -385,32 +397,25 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                     const bool in = act && qq >= 0 && qq < P;
                     v[r] = C{in ? x0[r] * sc : R(0), in && has1 ? x1[r] * sc : R(0)};
                 }
-            }
-            if (tt) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int a = h ? a1 : a0;
-                    R wbr[RR], wcr[RR];
+                if (tt) {
+                    R S00 = 0, S01 = 0, S10 = 0, S11 = 0;
+                    const R half = R(0.5) * (R)(P - 1);
 #pragma unroll
                     for (int r = 0; r < RR; ++r) {
                         const int qc = min(max(t + LW * r - o, 0), P - 1);
-                        wbr[r] = wb[a * P + qc];
-                        wcr[r] = wc[a * P + qc];
+                        const R y = ((R)qc - half) * fp.tt_delta;
+                        const R k0 = ((m0[r] >> (qc & 31)) & 1u) ? v[r].x : R(0);
+                        const R k1 = ((m1[r] >> (qc & 31)) & 1u) ? v[r].y : R(0);
+                        S00 += k0;
+                        S01 += y * k0;
+                        S10 += k1;
+                        S11 += y * k1;
                     }
-                    R sb = 0, scc = 0;
-#pragma unroll
-                    for (int r = 0; r < RR; ++r) {
-                        const R x = h ? v[r].y : v[r].x;
-                        sb += wbr[r] * x;
-                        scc += wcr[r] * x;
-                    }
-                    if (h) {
-                        s1b = sb;
-                        s1c = scc;
-                    } else {
-                        s0b = sb;
-                        s0c = scc;
-                    }
+                    const R xa0 = ((R)a0 - half) * fp.tt_delta, xa1 = ((R)a1 - half) * fp.tt_delta;
+                    s0b = (fp.tt_n[0] + fp.tt_n[1] * xa0) * S00 + fp.tt_n[2] * S01;
+                    s0c = (fp.tt_n[3] + fp.tt_n[4] * xa0) * S00 + fp.tt_n[5] * S01;
+                    s1b = (fp.tt_n[0] + fp.tt_n[1] * xa1) * S10 + fp.tt_n[2] * S11;
+                    s1c = (fp.tt_n[3] + fp.tt_n[4] * xa1) * S10 + fp.tt_n[5] * S11;
                 }
             }
             if (fp.any_tt) {  // per-row shares of the tip/tilt functionals
@@ -611,19 +616,15 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                             fp.energy[((size_t)gi * L + l0 + q) * Mh + k] = (float)(k == 0 ? e : R(2) * e);
                     }
                 }
-                // the slot's layers through one copy of the transform code
-#pragma unroll 1
-                for (int q = 0; q < LPS; ++q) {
-                    C x[RR];
+                // the slot's layers: their transforms interleaved
+                wfft_inv_n<M, LPS>(v, tw, t);
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) x[r] = (LPS == 1 || q == 0) ? v[0][r] : v[LPS - 1][r];
-                    wfft_inv<M>(x, tw, t);
+                for (int q = 0; q < LPS; ++q)
                     if (act && q < nl) {
                         C *dst = fp.w2 + ((((size_t)gi * L + l0 + q) * Mh + k) << LOGM);
 #pragma unroll
-                        for (int r = 0; r < RR; ++r) dst[t + LW * r] = x[r];
+                        for (int r = 0; r < RR; ++r) dst[t + LW * r] = v[q][r];
                     }
-                }
                 SAFR_MARK(12, k == b && u0 == 0);
             }
             SAFR_MARK(13, k == b);
@@ -982,6 +983,10 @@ struct Frame2Host {
         fp.rs_i0 = pl->d_rs_i0;
         fp.rs_w = (const R *)pl->d_rs_w;
         fp.tt_w = (const R *)pl->d_tt_w;
+        for (int i = 0; i < 6; ++i) fp.tt_n[i] = (R)pl->tt_n[i];
+        fp.tt_delta = (R)pl->delta;
+        fp.mask_bits = pl->d_mask_bits;
+        fp.mask_words = (pl->P + 31) / 32;
         fp.xy_hat = (const C *)pl->d_xy_hat;
         fp.pm = (R *)pl->d_pm;
         fp.bar = pl->d_bar;

@@ -122,6 +122,9 @@ struct safr_plan_s {
     int *d_rs_i0 = nullptr;
     void *d_rs_w = nullptr;
     unsigned char *d_mask = nullptr;
+    double tt_n[6] = {0, 0, 0, 0, 0, 0};  // rows b and c of the removeTT normal-equation inverse
+    std::vector<unsigned> mask_bits;      // [P][(P + 31) / 32] pupil mask, one bit per pixel
+    unsigned *d_mask_bits = nullptr;
     void *d_tt_w = nullptr;
     void *d_twq = nullptr;     // [M + min(M, 32)] warp-FFT twiddles of the persistent kernel
     void *d_xy_hat = nullptr;  // [2][Mh][M] DFT2 of x and y on the pupil mask (frequency-domain removeTT), j permuted

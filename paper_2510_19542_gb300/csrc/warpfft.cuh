@@ -182,4 +182,34 @@ __device__ __forceinline__ void wfft_inv(C (&v)[WShape<M>::R], const WTw<M, C> &
     dft_reg<S::R, true>(v);
 }
 
+// N independent inverse transforms in lockstep (the same steps, interleaved stage by
+// stage, so that one warp keeps N dependency chains in flight).
+template <int M, int N, typename C>
+__device__ __forceinline__ void wfft_inv_n(C (&v)[N][WShape<M>::R], const WTw<M, C> &w, int t)
+{
+    using S = WShape<M>;
+#pragma unroll 1
+    for (int h = 1; h < S::LW; h <<= 1) {
+        using R = decltype(C{}.x);
+        const bool low = (t & h) != 0;
+        const C ws = w.wlw[(t & (h - 1)) * (S::LW / (2 * h))];
+        const C wc = low ? C{ws.x, -ws.y} : C{R(1), R(0)};
+        const R sg = low ? R(-1) : R(1);
+#pragma unroll
+        for (int k = 0; k < S::R; ++k)
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                const C u = c_mul(v[n][k], wc);
+                const C p = shfl_xor_c(u, h);
+                v[n][k] = C{sg * u.x + p.x, sg * u.y + p.y};
+            }
+    }
+#pragma unroll
+    for (int n = 0; n < N; ++n) {
+#pragma unroll
+        for (int k = 1; k < S::R; ++k) v[n][k] = c_mulc(v[n][k], w.tw[k]);
+        dft_reg<S::R, true>(v[n]);
+    }
+}
+
 }  // namespace safr
