@@ -355,10 +355,10 @@ def measure_loop(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm):
            "frames_per_s": 1e3 / mean_ms,
            "latency_ms": {"p50": lat[len(lat) // 2],
                           "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
-           "launches_per_step": 1 + safr.safr_launches_per_frame(plan.handle) + (
-               0 if safr.safr_get_path(plan.handle) == safr.SAFR_PATH_FUSED else 1),
-           "integrator": "fused into the frame kernel's store" if safr.safr_get_path(plan.handle) ==
-           safr.SAFR_PATH_FUSED else "separate kernel",
+           "launches_per_step": 1 if safr.safr_get_path(plan.handle) == safr.SAFR_PATH_FUSED else
+           2 + safr.safr_launches_per_frame(plan.handle),
+           "fusion": "POLC as phase 0 and the integrator in the store of the frame kernel"
+           if safr.safr_get_path(plan.handle) == safr.SAFR_PATH_FUSED else "separate kernels",
            "polc_ms": t_polc, "integrate_ms": t_int,
            "algorithmic_bytes": nbytes, "frac_of_hbm": nbytes / (mean_ms * 1e-3) / 1e9 / hbm,
            "device_status": status, "steps": steps}

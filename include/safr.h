@@ -249,6 +249,18 @@ int safr_launches_per_frame(safr_plan_t plan);
  * (SAFR_PATH_FUSED or SAFR_PATH_PASSES), or -1 for a NULL plan.
  */
 safr_status safr_set_path(safr_plan_t plan, int path);
+
+/*
+ * CTAs of the persistent kernel (the paper fixes no launch shape): 0 (the
+ * default) is one per SM; a smaller grid leaves SMs free for another frame's
+ * kernel on another stream, and each phase's work is shared among the CTAs
+ * launched.  Values above the SM count mean one per SM.  The layers do not
+ * depend on it.  SAFR_ERR_UNSUPPORTED_SIZE (choice unchanged) when the plan
+ * has no persistent kernel or its shape does not fit the grid.
+ * safr_get_grid returns the CTAs of the next launch (0 for NULL).
+ */
+safr_status safr_set_grid(safr_plan_t plan, int ctas);
+int safr_get_grid(safr_plan_t plan);
 int safr_get_path(safr_plan_t plan);
 
 /*

@@ -601,8 +601,10 @@ safr_status safr_trace(safr_plan_t plan, int enable)
     if (enable && !plan->ev[0])
         for (auto &e : plan->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return SAFR_ERR_CUDA;
-    if (enable && !plan->d_stamps && plan->f2_grid > 0) {
-        const size_t nst = (size_t)plan->f2_grid * SAFR_TRACE_MARKS * sizeof(unsigned long long);
+    if (enable && !plan->d_stamps && plan->f2_grid > 0) {  // sized for one CTA per SM, the largest grid
+        int nsm = plan->f2_grid;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, plan->device);
+        const size_t nst = (size_t)std::max(nsm, plan->f2_grid) * SAFR_TRACE_MARKS * sizeof(unsigned long long);
         if (cudaMalloc((void **)&plan->d_stamps, nst) != cudaSuccess) return SAFR_ERR_OOM;
         if (cudaMemset(plan->d_stamps, 0, nst) != cudaSuccess) return SAFR_ERR_CUDA;
     }
@@ -684,6 +686,25 @@ safr_status safr_set_path(safr_plan_t plan, int path)
     plan->traced = 0;
     return SAFR_OK;
 }
+
+safr_status safr_set_grid(safr_plan_t plan, int ctas)
+{
+    if (!plan || ctas < 0) return SAFR_ERR_INVALID_ARG;
+    if (!plan->fused_ok) return SAFR_ERR_UNSUPPORTED_SIZE;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return SAFR_ERR_CUDA;
+    const int old = plan->f2_grid_force;
+    plan->f2_grid_force = ctas;
+    if (!safr::configure_fused(plan)) {  // the shape cannot run on that grid: keep the previous one
+        plan->f2_grid_force = old;
+        safr::configure_fused(plan);
+        return SAFR_ERR_UNSUPPORTED_SIZE;
+    }
+    plan->traced = 0;
+    return SAFR_OK;
+}
+
+int safr_get_grid(safr_plan_t plan) { return plan ? plan->f2_grid : 0; }
 
 int safr_get_path(safr_plan_t plan)
 {

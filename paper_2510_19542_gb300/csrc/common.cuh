@@ -51,6 +51,12 @@ __device__ __forceinline__ R load_in(const T *p) { return (R)to_real<T>(*p); }
 template <>
 __device__ __forceinline__ double load_in<double, double>(const double *p) { return *p; }
 
+// the same through L2 only (data another CTA of the same launch may have written)
+template <typename R, typename T>
+__device__ __forceinline__ R load_in_cg(const T *p) { return (R)to_real<T>(__ldcg(p)); }
+template <>
+__device__ __forceinline__ double load_in_cg<double, double>(const double *p) { return __ldcg(p); }
+
 template <typename R>
 __device__ __forceinline__ R block_sum(R v, R *red)
 {

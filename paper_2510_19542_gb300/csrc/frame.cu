@@ -22,6 +22,7 @@ bool configure_fused(safr_plan_s *pl)
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+    if (pl->f2_grid_force > 0 && pl->f2_grid_force < nsm) nsm = pl->f2_grid_force;  // safr_set_grid
     bool ok = false;
     if (pl->precision == SAFR_FP64)
         ok = frame2_configure_f64(pl, nsm);

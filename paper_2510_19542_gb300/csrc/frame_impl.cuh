@@ -75,6 +75,10 @@ struct Frame2Params {
     R inv_M2;
     int blend;                 // 1: out <- (1 - gain) out + gain layers (the AO loop's integrator)
     R gain;
+    // phase 0 of an AO loop step (polc_tab non-null): in <- mask (polc_psi + A(out)), the pseudo open
+    // loop data, from the POLC sample table of loop.cu; in is then the plan's staging buffer
+    const unsigned char *polc_tab;
+    const void *polc_psi;
     // shared-memory carve-up (bytes from the dynamic base)
     unsigned off_rs, off_tw, off_b, off_d, off_xy, off_s3;
     const void *in;
@@ -221,6 +225,41 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsig
 // faster than 32 warps with half the registers each at M = 256).
 __host__ __device__ constexpr int frame2_threads(int) { return 512; }
 
+// Phase 0 of an AO loop step: psi~_g = mask (psi_g + sum_l a_l(sample point)), bilinear in the
+// state a = out, one sample per thread over the whole grid (the sample table is described in
+// loop.cu).  Not inlined: its registers stay out of the frame's own allocation.
+template <int M, typename R, typename TIN, typename TOUT>
+__device__ __noinline__ void polc_phase(const Frame2Params<R> &fp, int G, int L, int P, int b, int nb)
+{
+    const size_t nn = (size_t)G * L * P;
+    const R *fx = (const R *)fp.polc_tab, *fy = fx + nn;
+    const int *ix = (const int *)(fy + nn), *iy = ix + nn;
+    const unsigned char *pmask = (const unsigned char *)(iy + nn);
+    const TIN *ps = (const TIN *)fp.polc_psi;
+    const TOUT *aa = (const TOUT *)fp.out;
+    TIN *dst = (TIN *)fp.in;
+    const int nth = blockDim.x;
+    for (long idx = (long)b * nth + threadIdx.x; idx < (long)G * P * P; idx += (long)nb * nth) {
+        const int g = (int)(idx / ((long)P * P)), pq = (int)(idx % ((long)P * P)), p = pq / P, q = pq % P;
+        R acc = 0;
+        if (pmask[pq]) {
+            acc = load_in<R>(ps + idx);
+#pragma unroll 8
+            for (int l = 0; l < L; ++l) {  // the layers' loads in flight together
+                const size_t k = ((size_t)g * L + l) * P;
+                const R fu = fx[k + p], fv = fy[k + q];
+                const int i0 = ix[k + p], j0 = iy[k + q];
+                const int i1 = i0 + 1 == M ? 0 : i0 + 1, j1 = j0 + 1 == M ? 0 : j0 + 1;
+                const TOUT *al = aa + (size_t)l * M * M;
+                const R v00 = (R)al[(size_t)i0 * M + j0], v01 = (R)al[(size_t)i0 * M + j1];
+                const R v10 = (R)al[(size_t)i1 * M + j0], v11 = (R)al[(size_t)i1 * M + j1];
+                acc += (R(1) - fu) * ((R(1) - fv) * v00 + fv * v01) + fu * ((R(1) - fv) * v10 + fv * v11);
+            }
+        }
+        dst[idx] = (TIN)acc;
+    }
+}
+
 // One frame of Algorithm 1 on the whole grid (all CTAs call it together).
 //   bar_base   grid barriers completed on fp.bar before this frame (thread 0)
 //   bph, tph   parities of the B and table mbarriers for this frame's first waits
@@ -354,6 +393,19 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         if (tma_pending) mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status);
     };
 
+    unsigned long long bar_next = bar_base;  // index of this frame's next grid barrier
+    // ---- phase 0 (AO loop step): pseudo open loop data ---------------------------
+    // psi~_g = mask (psi_g + sum_l a_l(sample point)), bilinear in the state a = out, one
+    // sample per thread over the whole grid; the samples' table is described in loop.cu
+    if (fp.polc_tab) {
+        polc_phase<M, R, TIN, TOUT>(fp, G, L, P, b, nb);
+        if (!grid_sync_bounded(fp.bar, bar_next, fp.status, fp.timeout_ns, &bar_flag, nullptr)) {
+            mbar_wait_bounded(&mbar_t, tph, fp.timeout_ns, fp.status);  // the table copies are not left in flight
+            return false;
+        }
+        ++bar_next;
+    }
+
     // ---- phase 1: row pairs ----------------------------------------------------
     {
         const int lo = (int)(((long long)b * fp.n1) / nb), hi = (int)(((long long)(b + 1) * fp.n1) / nb);
@@ -384,8 +436,8 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
 #pragma unroll
                 for (int r = 0; r < RR; ++r) {
                     const int qc = min(max(t + LW * r - o, 0), P - 1);
-                    x0[r] = load_in<R>(psi + (size_t)a0 * P + qc);
-                    x1[r] = load_in<R>(psi + (size_t)a1 * P + qc);
+                    x0[r] = load_in_cg<R>(psi + (size_t)a0 * P + qc);
+                    x1[r] = load_in_cg<R>(psi + (size_t)a1 * P + qc);
                     if (tt) {
                         m0[r] = mb0[qc >> 5];
                         m1[r] = mb1[qc >> 5];
@@ -473,7 +525,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         return false;
     }
     SAFR_MARK(5, true);
-    if (!grid_sync_bounded(fp.bar, bar_base, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 6 : nullptr)) {
+    if (!grid_sync_bounded(fp.bar, bar_next, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 6 : nullptr)) {
         drain();
         return false;
     }
@@ -643,7 +695,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         }
     }
     SAFR_MARK(14, true);
-    if (!grid_sync_bounded(fp.bar, bar_base + 1ull, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 15 : nullptr)) {
+    if (!grid_sync_bounded(fp.bar, bar_next + 1ull, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 15 : nullptr)) {
         drain();
         return false;
     }
@@ -829,7 +881,7 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
 {
     const unsigned long long base = bar_count_read(fp.bar);
     unsigned bph = 0;
-    if (frame_body<M, R, TIN, TOUT>(fp, base, bph, 0u, true)) bar_count_advance(fp.bar, base, 2u);
+    if (frame_body<M, R, TIN, TOUT>(fp, base, bph, 0u, true)) bar_count_advance(fp.bar, base, fp.polc_tab ? 3u : 2u);
 }
 
 // ----------------------------------------------------------------------------
@@ -965,6 +1017,8 @@ struct Frame2Host {
         fp.inv_M2 = (R)(1.0 / ((double)M * M));
         fp.blend = pl->loop_blend;
         fp.gain = (R)pl->loop_gain;
+        fp.polc_tab = pl->loop_polc_psi ? pl->d_polc : nullptr;
+        fp.polc_psi = pl->loop_polc_psi;
         fp.off_rs = pl->f2_off_rs;
         fp.off_tw = pl->f2_off_tw;
         fp.off_b = pl->f2_off_b;

@@ -233,15 +233,19 @@ safr_status safr_loop_step(safr_plan_t plan, const void *d_wavefronts, void *d_a
     if (!aligned16(d_wavefronts) || !aligned16(d_a)) return SAFR_ERR_MISALIGNED;
     LoopDeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
-    s = polc_launch(plan, d_wavefronts, d_a, plan->d_in_stage, stream);
-    if (s != SAFR_OK) return s;
-    if (safr::use_fused(plan)) {  // the persistent kernel blends its layers into the state as it stores them
+    if (safr::use_fused(plan)) {
+        // one launch: the persistent kernel computes the POLC data into the staging buffer (phase 0,
+        // one more grid barrier), reconstructs, and blends its layers into the state as it stores them
         plan->loop_blend = 1;
         plan->loop_gain = gain;
+        plan->loop_polc_psi = d_wavefronts;
         const cudaError_t e = safr::launch_fused(plan, plan->d_in_stage, nullptr, d_a, nullptr, stream);
         plan->loop_blend = 0;
+        plan->loop_polc_psi = nullptr;
         return e == cudaSuccess ? SAFR_OK : SAFR_ERR_CUDA;
     }
+    s = polc_launch(plan, d_wavefronts, d_a, plan->d_in_stage, stream);
+    if (s != SAFR_OK) return s;
     s = safr_reconstruct(plan, plan->d_in_stage, nullptr, plan->d_out_stage, nullptr, stream);
     if (s != SAFR_OK) return s;
     return integrate_launch(plan, plan->d_out_stage, d_a, gain, stream);

@@ -105,6 +105,7 @@ struct safr_plan_s {
     unsigned f2_off_rs = 0, f2_off_tw = 0, f2_off_b = 0, f2_off_d = 0, f2_off_s3 = 0, f2_off_xy = 0;
     size_t f2_smem = 0;
     int f2_rt_force = 0;        // phase-3 tile rows chosen by the autotuner (0: cost model)
+    int f2_grid_force = 0;      // CTAs of the persistent kernel (0: one per SM)
     int autotuned = 0;          // 1 after safr_autotune
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
@@ -135,6 +136,7 @@ struct safr_plan_s {
     unsigned char *d_polc = nullptr;  // POLC sample points on the output grid and the pupil (loop.cu)
     int loop_blend = 0;       // set by safr_loop_step around its persistent-kernel launch
     double loop_gain = 0;     // integrator gain of that launch
+    const void *loop_polc_psi = nullptr;  // wavefronts of that launch's POLC phase (null: no phase 0)
     int *d_status = nullptr;
     void *d_in_stage = nullptr, *d_out_stage = nullptr;
     float *d_in_scales_stage = nullptr, *d_out_scales_stage = nullptr;

@@ -40,7 +40,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
             "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
-            "safr_plan_save", "safr_plan_load", "safr_trace_stamps"]
+            "safr_plan_save", "safr_plan_load", "safr_trace_stamps", "safr_set_grid", "safr_get_grid"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -117,6 +117,8 @@ def load(build_if_missing: bool = True):
     lib.safr_trace_stamps.argtypes = [vp, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]
     lib.safr_set_path.argtypes = [vp, C.c_int]
     lib.safr_get_path.argtypes = [vp]
+    lib.safr_set_grid.argtypes = [vp, C.c_int]
+    lib.safr_get_grid.argtypes = [vp]
     lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
     lib.safr_destroy.argtypes = [vp]
     lib.safr_reconstruct_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -269,6 +271,15 @@ def safr_trace_phases(plan: int):
             "p2_star_fft", "p2_synced", "p2_B_landed", "p2_apply", "p2_inv_fft", "p2_stored", "p2_done",
             "bar2_arrive", "bar2_out", "p3_tables", "p3_staged", "p3_fft", "p3_synced", "p3_first_stored", "p3_done"]
     return dict(zip(keys, [us[i] for i in range(n.value)]))
+
+
+def safr_set_grid(plan: int, ctas: int):
+    """CTAs of the persistent kernel (0: one per SM)."""
+    _check(load().safr_set_grid(plan, int(ctas)), "safr_set_grid")
+
+
+def safr_get_grid(plan: int) -> int:
+    return load().safr_get_grid(plan)
 
 
 def safr_trace_stamps(plan: int) -> np.ndarray:
