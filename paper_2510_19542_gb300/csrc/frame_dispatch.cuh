@@ -8,14 +8,28 @@ namespace safr {
 
 template <typename R, typename TIN, typename TOUT, int M>
 struct Frame2Inst {
-    static void *kernel() { return (void *)k_frame2<M, R, TIN, TOUT>; }
-    static bool configure(safr_plan_s *pl, int nsm) { return Frame2Host<M, R>::configure(pl, nsm, kernel()); }
+    // the one-column-per-pass kernel, and (M >= 512 only) the two-column one
+    static void *kernel() { return (void *)k_frame2<M, R, TIN, TOUT, 1>; }
+    static void *kernel_ck(int ck)
+    {
+        if constexpr (M >= 512)
+            if (ck == 2) return (void *)k_frame2<M, R, TIN, TOUT, 2>;
+        return kernel();
+    }
+    static bool configure(safr_plan_s *pl, int nsm)
+    {
+        if (!Frame2Host<M, R>::configure(pl, nsm, kernel())) return false;
+        // the two-column instance needs the same shared-memory limit
+        if (pl->f2_ck == 2 && !smem_limit_allows(kernel_ck(2), pl->f2_smem)) pl->f2_ck = 1;
+        return true;
+    }
     static cudaError_t launch(safr_plan_s *pl, const void *in, const float *isc, void *out, float *osc,
                               cudaStream_t st)
     {
         Frame2Params<R> fp = Frame2Host<M, R>::params(pl, in, isc, out, osc);
         void *args[] = {&fp};
-        return cudaLaunchCooperativeKernel(kernel(), dim3(pl->f2_grid), dim3(frame2_threads(M)), args, pl->f2_smem, st);
+        return cudaLaunchCooperativeKernel(kernel_ck(pl->f2_ck), dim3(pl->f2_grid), dim3(frame2_threads(M)), args,
+                                           pl->f2_smem, st);
     }
 };
 

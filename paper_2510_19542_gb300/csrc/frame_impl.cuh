@@ -265,7 +265,7 @@ __device__ __noinline__ void polc_phase(const Frame2Params<R> &fp, int G, int L,
 //   bph, tph   parities of the B and table mbarriers for this frame's first waits
 //   first      the first frame of the launch: initialises the mbarriers
 // Returns false if a bounded wait gave up (status recorded); the caller then stops.
-template <int M, typename R, typename TIN, typename TOUT>
+template <int M, typename R, typename TIN, typename TOUT, int CKT>
 __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned long long bar_base, unsigned &bph,
                                            unsigned tph, bool first_frame)
 {
@@ -532,16 +532,22 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     SAFR_MARK(7, true);
 
     // ---- phase 2: columns --------------------------------------------------------
+    // CKT columns per pass (2 when B is read from global memory and the CTA has several
+    // columns): their star transforms share one round and their layer slots are packed
+    // into common rounds of the warps
     {
-        bool first_col = true;
-        for (int k = b; k < Mh; k += nb) {
-            // one transform per star: the column of w1 (p contiguous), forward FFT along p
+        constexpr int CK = CKT;
+        for (int kb = b; kb < Mh; kb += CK * nb) {
+            const bool first = kb == b;
+            const int ncols = min(CK, (Mh - 1 - kb) / nb + 1);
+            // one transform per (column, star): the column of w1 (p contiguous), forward FFT along p
+            const int ntask1 = ncols * G;
 #pragma unroll 1
-            for (int s0 = 0; s0 < G; s0 += UNITS) {
-                const int s = s0 + unit;
-                const bool act = s < G;
+            for (int s0 = 0; s0 < ntask1; s0 += UNITS) {
+                const int task = s0 + unit;
+                const bool act = task < ntask1;
                 if (!__any_sync(0xffffffffu, act)) continue;
-                const int ss = act ? s : 0;
+                const int tk = act ? task : 0, c = tk / G, ss = tk - c * G, k = kb + c * nb;
                 const C *src = fp.w1 + ((size_t)ss * Mh + k) * P;
                 C v[RR];
 #pragma unroll
@@ -552,7 +558,8 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                     if (!(act && pp >= 0 && pp < P)) v[r] = C{0, 0};
                 }
                 const bool tt = fp.any_tt && act && s_star_tt[ss];
-                if (first_col && fp.any_tt) {
+                R tb = 0, tc = 0;  // tip/tilt of the star
+                if (first && fp.any_tt) {  // from the row shares of phase 1 (every column of this pass)
                     R sb = 0, scs = 0;
                     if (tt)
                         for (int a0 = 0; a0 < P; a0 += LW * QC) {
@@ -574,10 +581,15 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                         sb += __shfl_xor_sync(0xffffffffu, sb, off);
                         scs += __shfl_xor_sync(0xffffffffu, scs, off);
                     }
-                    if (tt && t == 0) {  // tip/tilt of the star, for this CTA's later columns
+                    if (tt && c == 0 && t == 0) {  // for this CTA's later passes
                         s_ttb[ss] = sb;
                         s_ttc[ss] = scs;
                     }
+                    tb = sb;
+                    tc = scs;
+                } else if (tt) {
+                    tb = s_ttb[ss];
+                    tc = s_ttc[ss];
                 }
                 __syncwarp();
                 wfft_fwd<M>(v, tw, t);
@@ -586,47 +598,46 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                     for (int r = 0; r < RR; ++r) {
                         const int pos = r * LW + t;
                         C xh, yh;
-                        if (first_col && xy_pre) {
+                        if (first && c == 0 && xy_pre) {  // column b's spectra came with the prologue
                             xh = xys[pos];
                             yh = xys[M + pos];
                         } else {
                             xh = fp.xy_hat[((size_t)k << LOGM) + pos];
                             yh = fp.xy_hat[((size_t)(Mh + k) << LOGM) + pos];
                         }
-                        v[r].x -= s_ttb[ss] * xh.x + s_ttc[ss] * yh.x;
-                        v[r].y -= s_ttb[ss] * xh.y + s_ttc[ss] * yh.y;
+                        v[r].x -= tb * xh.x + tc * yh.x;
+                        v[r].y -= tb * xh.y + tc * yh.y;
                     }
                 }
                 if (act)
 #pragma unroll
-                    for (int r = 0; r < RR; ++r) Dp[(size_t)s * M + r * LW + t] = v[r];
+                    for (int r = 0; r < RR; ++r) Dp[((size_t)c * G + ss) * M + r * LW + t] = v[r];
             }
-            SAFR_MARK(8, k == b);
+            SAFR_MARK(8, first);
             __syncthreads();
-            SAFR_MARK(9, k == b);
-            const C *Bcol;
-            if (fp.stage_b) {
+            SAFR_MARK(9, first);
+            if (fp.stage_b) {  // one column per pass (ck = 1)
                 if (tid == 0) bar_flag = mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status) ? 1 : -1;
                 __syncthreads();
                 tma_pending = false;
                 bph ^= 1u;
                 if (bar_flag < 0) return false;  // the copy never landed: nothing in flight any more to wait for
-                Bcol = Bs;
-            } else {
-                Bcol = fp.B + (size_t)k * colB;
             }
-            SAFR_MARK(10, k == b);
-            // one transform slot per (group, LPS layers): b_l = sum_g B_lg d_g (permuted j) for
-            // the slot's layers from one read of d_g, then the inverse FFTs along j
-            const int per = (L + LPS - 1) / LPS, nslot = fp.ngroups * per;
-            for (int u0 = 0; u0 < nslot; u0 += UNITS) {
-                const int pt = u0 + unit;
-                const bool act = pt < nslot;
+            SAFR_MARK(10, first);
+            // one transform slot per (column, group, LPS layers): b_l = sum_g B_lg d_g (permuted j)
+            // for the slot's layers from one read of d_g, then the inverse FFTs along j
+            const int per = (L + LPS - 1) / LPS, nslot = fp.ngroups * per, ntask2 = ncols * nslot;
+            for (int u0 = 0; u0 < ntask2; u0 += UNITS) {
+                const int task = u0 + unit;
+                const bool act = task < ntask2;
                 if (!__any_sync(0xffffffffu, act)) continue;
-                const int ptk = act ? pt : 0, gi = ptk >= per ? 1 : 0, l0 = LPS * (ptk - gi * per);
+                const int tk = act ? task : 0, c = tk / nslot, ptk = tk - c * nslot, k = kb + c * nb;
+                const int gi = ptk >= per ? 1 : 0, l0 = LPS * (ptk - gi * per);
                 const int nl = min(LPS, L - l0);
                 const int gG = s_grp[gi].G;
+                const C *Bcol = fp.stage_b ? Bs : fp.B + (size_t)k * colB;
                 const C *Bl = Bcol + ((size_t)(s_grp[gi].b_row0 + l0 * gG) << LOGM);
+                const C *Dc = Dp + (size_t)c * G * M;
                 C v[LPS][RR];
 #pragma unroll
                 for (int q = 0; q < LPS; ++q)
@@ -635,7 +646,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 // B from shared memory (staged) by ld.shared, else from global memory
                 auto apply = [&](auto loadB) {
                     for (int gg = 0; gg < gG; ++gg) {
-                        const C *Dg = Dp + (size_t)s_grp[gi].star[gg] * M;
+                        const C *Dg = Dc + (size_t)s_grp[gi].star[gg] * M;
 #pragma unroll
                         for (int r = 0; r < RR; ++r) {
                             const int pos = r * LW + t;
@@ -655,7 +666,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 } else {
                     apply([&](size_t i) { return __ldcg(Bl + i); });
                 }
-                SAFR_MARK(11, k == b && u0 == 0);
+                SAFR_MARK(11, first && u0 == 0);
                 if (fp.energy) {  // Parseval partial sums of |b_l(j, k)|^2 over j
 #pragma unroll
                     for (int q = 0; q < LPS; ++q) {
@@ -677,21 +688,20 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
 #pragma unroll
                         for (int r = 0; r < RR; ++r) dst[t + LW * r] = v[q][r];
                     }
-                SAFR_MARK(12, k == b && u0 == 0);
+                SAFR_MARK(12, first && u0 == 0);
             }
-            SAFR_MARK(13, k == b);
-            // next column of this CTA: B block and column spectra are free once every warp is done
-            if (k + nb < Mh) {
+            SAFR_MARK(13, first);
+            // next pass of this CTA: B block and column spectra are free once every warp is done
+            if (kb + CK * nb < Mh) {
                 __syncthreads();
                 if (fp.stage_b) {
                     if (tid == 0) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        copy_b(k + nb);
+                        copy_b(kb + nb);
                     }
                     tma_pending = true;
                 }
             }
-            first_col = false;
         }
     }
     SAFR_MARK(14, true);
@@ -875,13 +885,14 @@ __device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsig
         asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(bar + 1), "l"(base + n) : "memory");
 }
 
-// One frame per launch.
-template <int M, typename R, typename TIN, typename TOUT>
+// One frame per launch; CK phase-2 columns per pass.
+template <int M, typename R, typename TIN, typename TOUT, int CK = 1>
 __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R> fp)
 {
     const unsigned long long base = bar_count_read(fp.bar);
     unsigned bph = 0;
-    if (frame_body<M, R, TIN, TOUT>(fp, base, bph, 0u, true)) bar_count_advance(fp.bar, base, fp.polc_tab ? 3u : 2u);
+    if (frame_body<M, R, TIN, TOUT, CK>(fp, base, bph, 0u, true))
+        bar_count_advance(fp.bar, base, fp.polc_tab ? 3u : 2u);
 }
 
 // ----------------------------------------------------------------------------
@@ -919,7 +930,10 @@ struct Frame2Host {
         pl->f2_off_tw = (unsigned)(any_rs ? al((size_t)M * (4 + rs)) : 0);
         pl->f2_off_b = (unsigned)rsb;
         pl->f2_off_d = (unsigned)(rsb + (stage ? al(colB) : 0));
-        pl->f2_off_xy = pl->f2_off_d + (unsigned)db;
+        // two phase-2 columns per pass: B read from global memory, CTAs with several columns,
+        // and a kernel instance that has it (M >= 512)
+        pl->f2_ck = (!stage && pl->f2_ck_allow && M >= 512 && Mh > nb && rsb + 2 * db + xyb <= limit) ? 2 : 1;
+        pl->f2_off_xy = pl->f2_off_d + (unsigned)(pl->f2_ck * db);
         const size_t s12 = pl->f2_off_xy + xyb;
         if (s12 > limit) return false;
         // phase 3 tiles: every CTA takes ceil(items / grid) items one after the

@@ -106,6 +106,8 @@ struct safr_plan_s {
     size_t f2_smem = 0;
     int f2_rt_force = 0;        // phase-3 tile rows chosen by the autotuner (0: cost model)
     int f2_grid_force = 0;      // CTAs of the persistent kernel (0: one per SM)
+    int f2_ck = 1;              // phase-2 columns per pass
+    int f2_ck_allow = 1;        // 0: one column per pass (schedule choice)
     int autotuned = 0;          // 1 after safr_autotune
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
