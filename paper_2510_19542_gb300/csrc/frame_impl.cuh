@@ -275,7 +275,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     constexpr int Mh = M / 2;
     constexpr int LOGM = S::LOG;
     constexpr int NTH = frame2_threads(M);
-    constexpr int LPS = NTH >= 1024 ? 1 : 2;  // layers per transform slot in the phase-2 apply
+    constexpr int LPS = (NTH >= 1024 || M >= 512) ? 1 : 2;  // layers per transform slot in the phase-2 apply
     constexpr int NW = NTH / 32;
     constexpr int UNITS = NW * S::TPW;  // transforms in flight per CTA
     constexpr int QC = 4;               // per-lane loads in flight in the pupil loops
@@ -429,40 +429,77 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             R s0b = 0, s0c = 0, s1b = 0, s1c = 0;
             const int a1 = has1 ? a0 + 1 : a0;
             {
-                R x0[RR], x1[RR];
-                unsigned m0[RR], m1[RR];
                 const unsigned *mb0 = fp.mask_bits + (size_t)a0 * fp.mask_words;
                 const unsigned *mb1 = fp.mask_bits + (size_t)a1 * fp.mask_words;
-#pragma unroll
-                for (int r = 0; r < RR; ++r) {
-                    const int qc = min(max(t + LW * r - o, 0), P - 1);
-                    x0[r] = load_in_cg<R>(psi + (size_t)a0 * P + qc);
-                    x1[r] = load_in_cg<R>(psi + (size_t)a1 * P + qc);
-                    if (tt) {
-                        m0[r] = mb0[qc >> 5];
-                        m1[r] = mb1[qc >> 5];
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < RR; ++r) {
-                    const int qq = t + LW * r - o;
-                    const bool in = act && qq >= 0 && qq < P;
-                    v[r] = C{in ? x0[r] * sc : R(0), in && has1 ? x1[r] * sc : R(0)};
-                }
-                if (tt) {
-                    R S00 = 0, S01 = 0, S10 = 0, S11 = 0;
-                    const R half = R(0.5) * (R)(P - 1);
+                R S00 = 0, S01 = 0, S10 = 0, S11 = 0;
+                const R half = R(0.5) * (R)(P - 1);
+                if constexpr (RR <= 8) {  // one batch of loads
+                    R x0[RR], x1[RR];
+                    unsigned m0[RR], m1[RR];
 #pragma unroll
                     for (int r = 0; r < RR; ++r) {
                         const int qc = min(max(t + LW * r - o, 0), P - 1);
-                        const R y = ((R)qc - half) * fp.tt_delta;
-                        const R k0 = ((m0[r] >> (qc & 31)) & 1u) ? v[r].x : R(0);
-                        const R k1 = ((m1[r] >> (qc & 31)) & 1u) ? v[r].y : R(0);
-                        S00 += k0;
-                        S01 += y * k0;
-                        S10 += k1;
-                        S11 += y * k1;
+                        x0[r] = load_in_cg<R>(psi + (size_t)a0 * P + qc);
+                        x1[r] = load_in_cg<R>(psi + (size_t)a1 * P + qc);
+                        if (tt) {
+                            m0[r] = mb0[qc >> 5];
+                            m1[r] = mb1[qc >> 5];
+                        }
                     }
+#pragma unroll
+                    for (int r = 0; r < RR; ++r) {
+                        const int qq = t + LW * r - o;
+                        const bool in = act && qq >= 0 && qq < P;
+                        v[r] = C{in ? x0[r] * sc : R(0), in && has1 ? x1[r] * sc : R(0)};
+                    }
+                    if (tt) {
+#pragma unroll
+                        for (int r = 0; r < RR; ++r) {
+                            const int qc = min(max(t + LW * r - o, 0), P - 1);
+                            const R y = ((R)qc - half) * fp.tt_delta;
+                            const R k0 = ((m0[r] >> (qc & 31)) & 1u) ? v[r].x : R(0);
+                            const R k1 = ((m1[r] >> (qc & 31)) & 1u) ? v[r].y : R(0);
+                            S00 += k0;
+                            S01 += y * k0;
+                            S10 += k1;
+                            S11 += y * k1;
+                        }
+                    }
+                } else {  // batches of 8 values (bounds the registers at large M)
+                    constexpr int RB = 8;
+#pragma unroll
+                    for (int r0 = 0; r0 < RR; r0 += RB) {
+                        R x0[RB], x1[RB];
+                        unsigned m0[RB], m1[RB];
+#pragma unroll
+                        for (int u = 0; u < RB; ++u) {
+                            const int qc = min(max(t + LW * (r0 + u) - o, 0), P - 1);
+                            x0[u] = load_in_cg<R>(psi + (size_t)a0 * P + qc);
+                            x1[u] = load_in_cg<R>(psi + (size_t)a1 * P + qc);
+                            if (tt) {
+                                m0[u] = mb0[qc >> 5];
+                                m1[u] = mb1[qc >> 5];
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < RB; ++u) {
+                            const int r = r0 + u, qq = t + LW * r - o;
+                            const bool in = act && qq >= 0 && qq < P;
+                            v[r] = C{in ? x0[u] * sc : R(0), in && has1 ? x1[u] * sc : R(0)};
+                            if (tt) {
+                                const int qc = min(max(qq, 0), P - 1);
+                                const R y = ((R)qc - half) * fp.tt_delta;
+                                const R k0 = ((m0[u] >> (qc & 31)) & 1u) ? v[r].x : R(0);
+                                const R k1 = ((m1[u] >> (qc & 31)) & 1u) ? v[r].y : R(0);
+                                S00 += k0;
+                                S01 += y * k0;
+                                S10 += k1;
+                                S11 += y * k1;
+                            }
+                        }
+                    }
+                }
+                if (tt) {
                     const R xa0 = ((R)a0 - half) * fp.tt_delta, xa1 = ((R)a1 - half) * fp.tt_delta;
                     s0b = (fp.tt_n[0] + fp.tt_n[1] * xa0) * S00 + fp.tt_n[2] * S01;
                     s0c = (fp.tt_n[3] + fp.tt_n[4] * xa0) * S00 + fp.tt_n[5] * S01;
@@ -783,26 +820,31 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 const bool hasb = 2 * i + 1 < (g1 ? nsrc1 : nsrc0);
                 // frequency k < M/2 reads stored column k; k > M/2 reads column M - k (conjugate
                 // symmetry); every lane loads from a valid address first, then selects
-                C v[RR], x1[RR], x2[RR];
+                C v[RR];
                 const int ib = hasb ? 2 * i + 1 : 2 * i;
+                constexpr int RB = RR < 8 ? RR : 8;  // values loaded per batch (bounds the registers at large M)
 #pragma unroll
-                for (int r = 0; r < RR; ++r) {
-                    const int k = r + RR * bt;
-                    const int kk = k < Mh ? k : (k > Mh ? M - k : 0);
-                    const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
-                    x1[r] = row[2 * i];
-                    x2[r] = row[ib];
-                }
+                for (int r0 = 0; r0 < RR; r0 += RB) {
+                    C x1[RB], x2[RB];
 #pragma unroll
-                for (int r = 0; r < RR; ++r) {
-                    const int k = r + RR * bt;
-                    C a = x1[r], c = hasb ? x2[r] : C{0, 0};
-                    if (k == 0) {
-                        a.y = 0;
-                        c.y = 0;
+                    for (int u = 0; u < RB; ++u) {
+                        const int k = r0 + u + RR * bt;
+                        const int kk = k < Mh ? k : (k > Mh ? M - k : 0);
+                        const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
+                        x1[u] = row[2 * i];
+                        x2[u] = row[ib];
                     }
-                    const C lo = C{a.x - c.y, a.y + c.x}, hi = C{a.x + c.y, c.x - a.y};
-                    v[r] = !act || k == Mh ? C{0, 0} : (k < Mh ? lo : hi);
+#pragma unroll
+                    for (int u = 0; u < RB; ++u) {
+                        const int k = r0 + u + RR * bt;
+                        C a = x1[u], c = hasb ? x2[u] : C{0, 0};
+                        if (k == 0) {
+                            a.y = 0;
+                            c.y = 0;
+                        }
+                        const C lo = C{a.x - c.y, a.y + c.x}, hi = C{a.x + c.y, c.x - a.y};
+                        v[r0 + u] = !act || k == Mh ? C{0, 0} : (k < Mh ? lo : hi);
+                    }
                 }
                 wfft_inv<M>(v, tw, t);
                 if (act)
