@@ -117,3 +117,26 @@ def test_loop_refuses_fp16_storage_plans():
         safr.safr_loop_step(plan.handle, x, a, 0.5)
     assert ei.value.status == safr.SAFR_ERR_UNSUPPORTED_SIZE
     plan.close()
+
+
+@pytest.mark.gpu
+def test_loop_steps_on_the_three_pass_schedule_match_oracle(oracle_mod):
+    """The same two iterations when the plan runs the three-pass schedule: POLC,
+    the frame and the integrator are then three separate kernels."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr, synth
+    dev = torch.device("cuda:0")
+    g = synth.scaled(synth.config(2), M=64, P=20)
+    plan = safr.Plan(g, device=0, path=safr.SAFR_PATH_PASSES)
+    orc = oracle_mod.OraclePlan(g)
+    L, M = len(g["h"]), g["M"]
+    a_ref = np.random.default_rng(6).standard_normal((L, M, M)).astype(np.float32).astype(np.float64) * 0.1
+    a = torch.from_numpy(a_ref.astype(np.float32)).to(dev)
+    for seed in (41, 42):
+        psi = synth.frame(g, seed=seed).astype(np.float32)
+        safr.safr_loop_step(plan.handle, torch.from_numpy(psi).to(dev), a, 0.25)
+        a_ref = oracle_mod.integrate(orc.reconstruct(oracle_mod.polc(g, psi.astype(np.float64), a_ref)), a_ref, 0.25)
+        assert _rel(a.double().cpu().numpy(), a_ref) <= 1e-5
+    assert safr.safr_get_status(plan.handle) == 0
+    plan.close()
