@@ -15,6 +15,7 @@
 // The Nyquist row j = M/2 is zero (and the Nyquist column k = M/2 is not stored).
 #include <cuda_runtime.h>
 
+#include "common.cuh"
 #include "freqorder.h"
 #include "plan.h"
 
@@ -27,10 +28,14 @@ __device__ __forceinline__ void store_c<float2>(float2 *p, double re, double im)
 template <>
 __device__ __forceinline__ void store_c<double2>(double2 *p, double re, double im) { *p = make_double2(re, im); }
 
-template <typename C>
+// CACHE: s_l(n) and the phase factors of A_n, computed once in the first pass, are kept in
+// shared memory for the solves (element e of thread t at [e * blockDim + t]); otherwise the
+// solves evaluate them again (large G * L).
+template <typename C, bool CACHE>
 __global__ void __launch_bounds__(128) precompute_kernel(int M, int Mh, int sumLG, double beta, PreGroupDev gr, C *B,
                                                          int *status)
 {
+    extern __shared__ double pc_cache[];
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (long)M * Mh) return;
     const int j = (int)(idx % M), k = (int)(idx / M);
@@ -50,11 +55,20 @@ __global__ void __launch_bounds__(128) precompute_kernel(int M, int Mh, int sumL
     double Kr[SAFR_MAX_GROUP_G][SAFR_MAX_GROUP_G], Ki[SAFR_MAX_GROUP_G][SAFR_MAX_GROUP_G];
     for (int g = 0; g < G; ++g)
         for (int h = 0; h < G; ++h) Kr[g][h] = Ki[g][h] = 0.0;
+    const int nt = blockDim.x, tl = threadIdx.x;
+    double *cs_ = pc_cache, *sn_ = pc_cache + (size_t)G * L * nt, *s_ = pc_cache + 2 * (size_t)G * L * nt;
     for (int l = 0; l < L; ++l) {
         const double s = gr.sw[l] * pow(1.0 + gr.tau[l] * n2, -0.5 * beta);
         const double s2 = s * s;
         double cr[SAFR_MAX_GROUP_G], ci[SAFR_MAX_GROUP_G];
         for (int g = 0; g < G; ++g) sincospi(twoM * (nx * gr.sx[g * L + l] + ny * gr.sy[g * L + l]), &ci[g], &cr[g]);
+        if constexpr (CACHE) {
+            s_[(size_t)l * nt + tl] = s;
+            for (int g = 0; g < G; ++g) {
+                cs_[((size_t)g * L + l) * nt + tl] = cr[g];
+                sn_[((size_t)g * L + l) * nt + tl] = ci[g];
+            }
+        }
         for (int g = 0; g < G; ++g)
             for (int h = 0; h <= g; ++h) {
                 // e^{i th_g} e^{-i th_h}
@@ -88,13 +102,22 @@ __global__ void __launch_bounds__(128) precompute_kernel(int M, int Mh, int sumL
 
     // every layer: solve K x = a_l, B_lg = s_l conj(x_g)
     for (int l = 0; l < L; ++l) {
-        const double s = gr.sw[l] * pow(1.0 + gr.tau[l] * n2, -0.5 * beta);
+        double s;
         double yr[SAFR_MAX_GROUP_G], yi[SAFR_MAX_GROUP_G];
-        for (int g = 0; g < G; ++g) {
-            double sn, cs;
-            sincospi(twoM * (nx * gr.sx[g * L + l] + ny * gr.sy[g * L + l]), &sn, &cs);
-            yr[g] = s * cs;
-            yi[g] = s * sn;
+        if constexpr (CACHE) {
+            s = s_[(size_t)l * nt + tl];
+            for (int g = 0; g < G; ++g) {
+                yr[g] = s * cs_[((size_t)g * L + l) * nt + tl];
+                yi[g] = s * sn_[((size_t)g * L + l) * nt + tl];
+            }
+        } else {
+            s = gr.sw[l] * pow(1.0 + gr.tau[l] * n2, -0.5 * beta);
+            for (int g = 0; g < G; ++g) {
+                double sn, cs;
+                sincospi(twoM * (nx * gr.sx[g * L + l] + ny * gr.sy[g * L + l]), &sn, &cs);
+                yr[g] = s * cs;
+                yi[g] = s * sn;
+            }
         }
         // forward: C y = a
         for (int r = 0; r < G; ++r) {
@@ -120,12 +143,29 @@ __global__ void __launch_bounds__(128) precompute_kernel(int M, int Mh, int sumL
     }
 }
 
+template <typename C>
+cudaError_t launch_group(const safr_plan_s *plan, const PreGroupDev &d, long n, cudaStream_t stream)
+{
+    // threads per block so that the cache (2 G L + L doubles per thread) fits in 200 KB; below 32, no cache
+    const size_t per = (2 * (size_t)d.G * d.L + d.L) * sizeof(double);
+    int threads = 128;
+    while (threads >= 32 && per * threads > 200 * 1024) threads /= 2;
+    if (threads >= 32 && smem_limit_allows((const void *)precompute_kernel<C, true>, per * threads)) {
+        const int blocks = (int)((n + threads - 1) / threads);
+        precompute_kernel<C, true><<<blocks, threads, per * threads, stream>>>(plan->M, plan->Mh, plan->sumLG, plan->beta,
+                                                                             d, (C *)plan->d_B, plan->d_status);
+    } else {
+        const int blocks = (int)((n + 127) / 128);
+        precompute_kernel<C, false><<<blocks, 128, 0, stream>>>(plan->M, plan->Mh, plan->sumLG, plan->beta, d,
+                                                                (C *)plan->d_B, plan->d_status);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_precompute(safr_plan_s *plan, cudaStream_t stream)
 {
     const int M = plan->M, Mh = plan->Mh, L = plan->L;
     const long n = (long)M * Mh;
-    const int threads = 128;
-    const int blocks = (int)((n + threads - 1) / threads);
     size_t off = 0;
     for (int gi = 0; gi < plan->ngroups; ++gi) {
         const Group &g = plan->grp[gi];
@@ -139,13 +179,8 @@ cudaError_t launch_precompute(safr_plan_s *plan, cudaStream_t stream)
         d.sw = d.sy + (size_t)g.G * L;
         d.tau = d.sw + L;
         off += 2 * (size_t)g.G * L + 2 * L;
-        if (plan->precision == SAFR_FP64)
-            precompute_kernel<double2><<<blocks, threads, 0, stream>>>(M, Mh, plan->sumLG, plan->beta, d,
-                                                                       (double2 *)plan->d_B, plan->d_status);
-        else
-            precompute_kernel<float2><<<blocks, threads, 0, stream>>>(M, Mh, plan->sumLG, plan->beta, d,
-                                                                      (float2 *)plan->d_B, plan->d_status);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = plan->precision == SAFR_FP64 ? launch_group<double2>(plan, d, n, stream)
+                                                       : launch_group<float2>(plan, d, n, stream);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
