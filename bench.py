@@ -509,6 +509,26 @@ def measure_learned(safr, synth, torch, dev, stream, steps, warmup, flush_l2):
 
 
 # ----------------------------------------------------------------------------
+# ranks (one process per GPU, replicas: no collective on the data path)
+# ----------------------------------------------------------------------------
+def rank_max(value: float, device) -> float:
+    """The largest of the ranks' values (a timed region's wall, max over ranks)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, total_ms_max: float) -> float:
+    """Whole-job frames/s: every rank reconstructs `steps` frames of its own; the
+    job takes the slowest rank's time."""
+    return world * steps / (total_ms_max * 1e-3)
+
+
+# ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
 def run_safr(args):
@@ -592,11 +612,7 @@ def run_safr(args):
         _, ph = one(i, True)
         phases.append(ph)
     safr.safr_trace(plan.handle, False)
-    total_ms = float(np.sum(lat))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = rank_max(float(np.sum(lat)), dev)
     status = safr.safr_get_status(plan.handle)
 
     # end to end through the public host-buffer entry point (pinned memory)
@@ -611,10 +627,7 @@ def run_safr(args):
         t0 = time.perf_counter()
         safr.safr_reconstruct_host(plan.handle, hin[i % 8], hout, stream=stream)
         e2e_ms += 1e3 * (time.perf_counter() - t0)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = rank_max(e2e_ms, dev)
 
     # the last timed frame against the FP64 oracle
     rel_l2 = None
@@ -685,7 +698,7 @@ def run_safr(args):
         except (OSError, ValueError, KeyError):
             traffic = None
         lat_sorted = sorted(lat)
-        value = world * args.steps / (total_ms * 1e-3)
+        value = job_throughput(world, args.steps, total_ms)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -704,7 +717,7 @@ def run_safr(args):
                          "algorithmic_bytes": k_bytes},
             "clocks": clk, "gpu_launches": launches * args.steps, "device_status": status,
             "rel_l2_vs_oracle": rel_l2,
-            "e2e": {"value": world * args.steps / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": job_throughput(world, args.steps, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
                     "ms_per_step": e2e_ms / args.steps},
             "wall_s_timed_region": wall,
