@@ -168,11 +168,14 @@ safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const f
                              void *d_layers, float *d_out_scales, cudaStream_t stream);
 
 /*
- * End-to-end form of safr_reconstruct for host buffers: copies the frame from
- * `h_wavefronts` (and `h_in_scales`) to plan-owned device staging buffers,
- * reconstructs, copies the layers (and scales) back to `h_layers` /
- * `h_out_scales`, and synchronises `stream` before returning.  Page-locked
- * host memory makes the copies asynchronous DMA; pageable memory also works.
+ * End-to-end form of safr_reconstruct for host buffers, synchronising
+ * `stream` before returning.  When every buffer is page-locked, mapped host
+ * memory (cudaHostAlloc, cudaHostRegister) aligned to 16 bytes, the kernels
+ * read the frame from `h_wavefronts` (and `h_in_scales`) and write the layers
+ * (and scales) to `h_layers` / `h_out_scales` in place over the host link
+ * (NVLink-C2C on Grace), with no staging copies.  Otherwise the frame is
+ * copied to plan-owned device staging buffers, reconstructed, and copied
+ * back; pageable memory works that way.
  */
 safr_status safr_reconstruct_host(safr_plan_t plan, const void *h_wavefronts, const float *h_in_scales,
                                   void *h_layers, float *h_out_scales, cudaStream_t stream);

@@ -487,6 +487,20 @@ safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const f
     return SAFR_OK;
 }
 
+// The device address of a page-locked, mapped host buffer (16-byte aligned), else null: the GPU
+// then reads and writes it directly over the host link (NVLink-C2C on Grace) without staging copies.
+const void *host_alias(const void *h)
+{
+    if (!h) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer || !aligned16(a.devicePointer)) return nullptr;
+    return a.devicePointer;
+}
+
 safr_status safr_reconstruct_host(safr_plan_t plan, const void *h_wavefronts, const float *h_in_scales,
                                   void *h_layers, float *h_out_scales, cudaStream_t stream)
 {
@@ -498,6 +512,16 @@ safr_status safr_reconstruct_host(safr_plan_t plan, const void *h_wavefronts, co
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
     const size_t nsc_in = (size_t)plan->G * sizeof(float), nsc_out = (size_t)plan->L * sizeof(float);
+    {  // page-locked buffers: the kernels read and write them in place
+        const void *din = host_alias(h_wavefronts), *dout = host_alias(h_layers);
+        const void *dsi = host_alias(h_in_scales), *dso = host_alias(h_out_scales);
+        if (din && dout && (!h_in_scales || dsi) && (!h_out_scales || dso)) {
+            if (dispatch(plan, din, (const float *)dsi, (void *)dout, (float *)dso, stream) != cudaSuccess ||
+                cudaStreamSynchronize(stream) != cudaSuccess)
+                return SAFR_ERR_CUDA;
+            return SAFR_OK;
+        }
+    }
     if (cudaMemcpyAsync(plan->d_in_stage, h_wavefronts, plan->in_bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess)
         return SAFR_ERR_CUDA;
     if (h_in_scales && cudaMemcpyAsync(plan->d_in_scales_stage, h_in_scales, nsc_in, cudaMemcpyHostToDevice,
