@@ -304,6 +304,7 @@ def measure_batch(safr, synth, torch, dev, stream, steps, warmup, flush_l2, hbm,
     out = {"frames": n, "grids": sorted({g["M"] for g in geoms}), "stars": [3, 9], "layers": [3, 35],
            "precision": "fp32", "frames_per_s": n / (mb * 1e-3), "ms_per_batch": mb,
            "launches_per_batch": safr.safr_batch_launches(batch), "graph": safr.safr_batch_graph(batch),
+           "concurrent_chains": safr.safr_batch_chains(batch),
            "autotuned_paths": {
                "fused": paths.count(safr.SAFR_PATH_FUSED), "passes": paths.count(safr.SAFR_PATH_PASSES)},
            "algorithmic_bytes_per_batch": nbytes, "frac_of_hbm": nbytes / (mb * 1e-3) / 1e9 / hbm,

@@ -5,6 +5,8 @@
 // cooperative kernel, or the three passes) are captured into ONE CUDA graph;
 // each call replays it with a single graph launch.  The graph bakes in the
 // frames' buffer pointers, so a call with other pointers captures it again.
+// Frames of grids up to 256 may run on K concurrent chains of the graph, each
+// on 1/K of the SMs; K in {1, 2, 4} is timed at the first capture.
 //
 // A single persistent launch that loops over a device array of frame
 // parameters was built and measured slower than this graph (4.49 ms against
@@ -76,6 +78,9 @@ struct safr_batch_s {
     bool graph_failed = false;
     std::vector<const void *> key;  // buffer pointers and schedules the graph was captured with
     cudaStream_t cap = nullptr;
+    int chains = 0;                    // concurrent chains of the graph (0: not chosen yet)
+    std::vector<cudaStream_t> side;    // capture-side streams of chains 1..
+    std::vector<cudaEvent_t> ev;       // fork / join events
 };
 
 namespace {
@@ -92,29 +97,173 @@ safr_status enqueue_frames(safr_batch_s *b, const void *const *in, const float *
     return SAFR_OK;
 }
 
-// Capture the frames' launches into a graph (trace events left out).
-void capture(safr_batch_s *b, const void *const *in, const float *const *isc, void *const *out, float *const *osc)
+// Frames that may run K at a time: persistent-kernel plans of grids up to 256 (latency-bound: on
+// 1/K of the SMs each, K of them finish sooner than one after the other).  Larger frames run alone
+// on the whole GPU.  A plan that appears twice keeps the batch sequential.
+bool concurrent_frame(const safr_plan_s *pl) { return safr::use_fused(pl) && pl->M <= 256; }
+
+int concurrent_count(const safr_batch_s *b)
 {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    b->exec = nullptr;
-    b->graph_failed = true;
+    std::vector<const safr_plan_s *> seen;
+    int n = 0;
+    for (const safr_plan_s *pl : b->plans) {
+        if (std::find(seen.begin(), seen.end(), pl) != seen.end()) return 0;
+        seen.push_back(pl);
+        n += concurrent_frame(pl) ? 1 : 0;
+    }
+    return n;
+}
+
+// Capture the frames' launches into a graph (trace events left out).  K = 1: one chain, frame after
+// frame.  K > 1: the large frames one after the other, then the concurrent frames on K chains at
+// 1/K of the SMs each, assigned greedily by an estimate of their cost.
+bool capture_k(safr_batch_s *b, int K, const void *const *in, const float *const *isc, void *const *out,
+               float *const *osc, cudaGraphExec_t *exec_out)
+{
+    *exec_out = nullptr;
     std::vector<int> trace(b->n);
     for (int i = 0; i < b->n; ++i) {
         trace[i] = b->plans[i]->trace;
         b->plans[i]->trace = 0;
     }
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device);
+    // the concurrent frames' plans on 1/K of the SMs, with their phase-3 tiling kept (every layer
+    // sample is then computed by the same arithmetic as on the plan's own grid); set up before the
+    // capture and put back after it (the captured launches keep their own copies of the parameters)
+    struct Saved {
+        safr_plan_s *pl;
+        int grid, rt;
+    };
+    std::vector<Saved> saved;
+    bool conf_ok = true;
+    if (K > 1)
+        for (safr_plan_s *pl : b->plans)
+            if (concurrent_frame(pl)) {
+                saved.push_back({pl, pl->f2_grid_force, pl->f2_rt_force});
+                pl->f2_grid_force = nsm / K;
+                pl->f2_rt_force = pl->f2_rt3;
+                conf_ok = conf_ok && safr::configure_fused(pl) && safr::use_fused(pl);
+            }
     cudaGraph_t graph = nullptr;
-    if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        const safr_status s = enqueue_frames(b, in, isc, out, osc, b->cap);
+    bool ok = false;
+    if (conf_ok && cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        safr_status s = SAFR_OK;
+        if (K <= 1) {
+            s = enqueue_frames(b, in, isc, out, osc, b->cap);
+        } else {
+            for (int i = 0; i < b->n && s == SAFR_OK; ++i)
+                if (!concurrent_frame(b->plans[i]))
+                    s = safr_reconstruct(b->plans[i], in[i], isc ? isc[i] : nullptr, out[i], osc ? osc[i] : nullptr,
+                                         b->cap);
+            // fork: chains 1..K-1 start after the large frames
+            if (s == SAFR_OK && cudaEventRecord(b->ev[0], b->cap) != cudaSuccess) s = SAFR_ERR_CUDA;
+            for (int c = 1; c < K && s == SAFR_OK; ++c)
+                if (cudaStreamWaitEvent(b->side[c - 1], b->ev[0], 0) != cudaSuccess) s = SAFR_ERR_CUDA;
+            // greedy: largest frames first, each to the chain with the least work so far
+            std::vector<int> idx;
+            for (int i = 0; i < b->n; ++i)
+                if (concurrent_frame(b->plans[i])) idx.push_back(i);
+            auto cost = [&](int i) {
+                const safr_plan_s *pl = b->plans[i];
+                return (double)pl->M * pl->M * (pl->sumLG + pl->L + pl->G);
+            };
+            std::sort(idx.begin(), idx.end(), [&](int x, int y) { return cost(x) > cost(y); });
+            std::vector<double> load(K, 0.0);
+            for (int i : idx) {
+                if (s != SAFR_OK) break;
+                const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[c] += cost(i);
+                s = safr_reconstruct(b->plans[i], in[i], isc ? isc[i] : nullptr, out[i], osc ? osc[i] : nullptr,
+                                     c == 0 ? b->cap : b->side[c - 1]);
+            }
+            // join
+            for (int c = 1; c < K && s == SAFR_OK; ++c)
+                if (cudaEventRecord(b->ev[c], b->side[c - 1]) != cudaSuccess ||
+                    cudaStreamWaitEvent(b->cap, b->ev[c], 0) != cudaSuccess)
+                    s = SAFR_ERR_CUDA;
+        }
         const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
-        if (s == SAFR_OK && e == cudaSuccess && graph && cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess)
-            b->graph_failed = false;
-        else
-            b->exec = nullptr;
+        ok = s == SAFR_OK && e == cudaSuccess && graph && cudaGraphInstantiate(exec_out, graph, 0) == cudaSuccess;
+        if (!ok) *exec_out = nullptr;
         if (graph) cudaGraphDestroy(graph);
     }
     cudaGetLastError();
+    for (const Saved &v : saved) {
+        v.pl->f2_grid_force = v.grid;
+        v.pl->f2_rt_force = v.rt;
+        safr::configure_fused(v.pl);
+    }
+    cudaGetLastError();
     for (int i = 0; i < b->n; ++i) b->plans[i]->trace = trace[i];
+    return ok;
+}
+
+// Median time of three replays (after one) of a captured batch on the capture stream, in ms; < 0 on error.
+float time_graph(safr_batch_s *b, cudaGraphExec_t ex)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0f;
+    std::vector<float> t;
+    for (int r = 0; r < 4; ++r) {
+        float ms = -1.0f;
+        if (cudaEventRecord(e0, b->cap) != cudaSuccess || cudaGraphLaunch(ex, b->cap) != cudaSuccess ||
+            cudaEventRecord(e1, b->cap) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+            ms = -1.0f;
+        if (r > 0) t.push_back(ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::sort(t.begin(), t.end());
+    return t[0] < 0 ? -1.0f : t[1];
+}
+
+// (Re)capture the batch's graph.  The first time, every chain count K in {1, 2, 4} that the batch
+// can use is captured and timed, and the fastest is kept for later captures.
+void capture(safr_batch_s *b, const void *const *in, const float *const *isc, void *const *out, float *const *osc)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_failed = true;
+    const int nconc = concurrent_count(b);
+    if (b->side.empty() && nconc >= 2) {  // streams and events of up to 4 chains
+        b->side.assign(3, nullptr);
+        b->ev.assign(4, nullptr);
+        bool ok = true;
+        for (auto &st : b->side) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+        for (auto &e : b->ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            b->chains = 1;
+        }
+    }
+    if (nconc < 2) b->chains = 1;
+    if (b->chains == 0) {
+        int best_k = 1;
+        float best_t = -1.0f;
+        cudaGraphExec_t best = nullptr;
+        for (int K : {1, 2, 4}) {
+            if (K > 1 && nconc < K) continue;
+            cudaGraphExec_t ex = nullptr;
+            if (!capture_k(b, K, in, isc, out, osc, &ex)) continue;
+            const float t = time_graph(b, ex);
+            if (t >= 0.0f && (best_t < 0.0f || t < best_t)) {
+                if (best) cudaGraphExecDestroy(best);
+                best = ex;
+                best_t = t;
+                best_k = K;
+            } else {
+                cudaGraphExecDestroy(ex);
+            }
+        }
+        b->chains = best_k;
+        b->exec = best;
+    } else {
+        capture_k(b, b->chains, in, isc, out, osc, &b->exec);
+    }
+    b->graph_failed = b->exec == nullptr;
+    cudaGetLastError();
 }
 
 }  // namespace
@@ -205,6 +354,8 @@ int safr_batch_launches(safr_batch_t b)
 
 int safr_batch_graph(safr_batch_t b) { return b && b->exec ? 1 : 0; }
 
+int safr_batch_chains(safr_batch_t b) { return b ? b->chains : 0; }
+
 safr_status safr_batch_destroy(safr_batch_t b)
 {
     if (!b) return SAFR_ERR_INVALID_ARG;
@@ -213,6 +364,10 @@ safr_status safr_batch_destroy(safr_batch_t b)
         cudaDeviceSynchronize();
         if (b->exec) cudaGraphExecDestroy(b->exec);
         if (b->cap) cudaStreamDestroy(b->cap);
+        for (auto st : b->side)
+            if (st) cudaStreamDestroy(st);
+        for (auto e : b->ev)
+            if (e) cudaEventDestroy(e);
     }
     delete b;
     return SAFR_OK;

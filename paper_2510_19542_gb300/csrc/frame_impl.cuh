@@ -99,7 +99,7 @@ struct Frame2Params {
     int mask_words;
     const C *xy_hat;           // [2][M/2][M], j in the permuted order
     R *pm;                     // [G][P][2]
-    unsigned long long *bar;   // [2] arrival count, grid barriers completed before the launch
+    unsigned long long *bar;   // [2] arrival count, and the arrival count when the previous launch ended
     unsigned long long *stamps;
     int *status;
     int star_tt[SAFR_MAX_G];
@@ -200,7 +200,7 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsig
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned long long target = (index + 1ull) * gridDim.x;
+        const unsigned long long target = index + gridDim.x;  // index: arrivals counted before this barrier
         asm volatile("red.release.gpu.global.add.u64 [%0], 1;" ::"l"(bar) : "memory");
         if (arrive_mark) *arrive_mark = gtimer();
         int ok = 1;
@@ -261,7 +261,7 @@ __device__ __noinline__ void polc_phase(const Frame2Params<R> &fp, int G, int L,
 }
 
 // One frame of Algorithm 1 on the whole grid (all CTAs call it together).
-//   bar_base   grid barriers completed on fp.bar before this frame (thread 0)
+//   bar_base   arrivals counted on fp.bar before this frame (thread 0)
 //   bph, tph   parities of the B and table mbarriers for this frame's first waits
 //   first      the first frame of the launch: initialises the mbarriers
 // Returns false if a bounded wait gave up (status recorded); the caller then stops.
@@ -393,7 +393,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         if (tma_pending) mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status);
     };
 
-    unsigned long long bar_next = bar_base;  // index of this frame's next grid barrier
+    unsigned long long bar_next = bar_base;  // arrivals counted before this frame's next grid barrier
     // ---- phase 0 (AO loop step): pseudo open loop data ---------------------------
     // psi~_g = mask (psi_g + sum_l a_l(sample point)), bilinear in the state a = out, one
     // sample per thread over the whole grid; the samples' table is described in loop.cu
@@ -403,7 +403,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             mbar_wait_bounded(&mbar_t, tph, fp.timeout_ns, fp.status);  // the table copies are not left in flight
             return false;
         }
-        ++bar_next;
+        bar_next += nb;
     }
 
     // ---- phase 1: row pairs ----------------------------------------------------
@@ -742,7 +742,8 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         }
     }
     SAFR_MARK(14, true);
-    if (!grid_sync_bounded(fp.bar, bar_next + 1ull, fp.status, fp.timeout_ns, &bar_flag, stamp ? stamp + 15 : nullptr)) {
+    if (!grid_sync_bounded(fp.bar, bar_next + (unsigned long long)nb, fp.status, fp.timeout_ns, &bar_flag,
+                           stamp ? stamp + 15 : nullptr)) {
         drain();
         return false;
     }
@@ -912,19 +913,20 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     return true;
 }
 
-// Reads the barrier count of the counter at the start of a launch (thread 0).
-// The previous launch on the counter wrote it; stream order makes that write
-// visible, so a plain load does (an acquire load would stall thread 0 until it
-// lands).  After its last grid barrier, CTA 0 stores the count plus the number
-// of barriers of this launch: every CTA has read the old value by then.
+// Reads, at the start of a launch (thread 0), the arrival count the counter held when the previous
+// launch on it ended.  That launch wrote it; stream order makes the write visible, so a plain load
+// does (an acquire load would stall thread 0 until it lands).  After its last grid barrier, CTA 0
+// stores the count plus this launch's arrivals (barriers x its own grid): every CTA has read the old
+// value by then, and the next launch may use another grid size.
 __device__ __forceinline__ unsigned long long bar_count_read(const unsigned long long *bar)
 {
     return threadIdx.x == 0 ? __ldcg(bar + 1) : 0ull;
 }
-__device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsigned long long base, unsigned n)
+__device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsigned long long base,
+                                                  unsigned long long arrivals)
 {
     if (blockIdx.x == 0 && threadIdx.x == 0)
-        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(bar + 1), "l"(base + n) : "memory");
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(bar + 1), "l"(base + arrivals) : "memory");
 }
 
 // One frame per launch; CK phase-2 columns per pass.
@@ -934,7 +936,7 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     const unsigned long long base = bar_count_read(fp.bar);
     unsigned bph = 0;
     if (frame_body<M, R, TIN, TOUT, CK>(fp, base, bph, 0u, true))
-        bar_count_advance(fp.bar, base, fp.polc_tab ? 3u : 2u);
+        bar_count_advance(fp.bar, base, (fp.polc_tab ? 3ull : 2ull) * gridDim.x);
 }
 
 // ----------------------------------------------------------------------------

@@ -40,7 +40,8 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_batch_create", "safr_batch_reconstruct", "safr_batch_get_status", "safr_batch_launches",
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
             "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
-            "safr_plan_save", "safr_plan_load", "safr_trace_stamps", "safr_set_grid", "safr_get_grid"]
+            "safr_plan_save", "safr_plan_load", "safr_trace_stamps", "safr_set_grid", "safr_get_grid",
+            "safr_batch_chains"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -128,6 +129,7 @@ def load(build_if_missing: bool = True):
     lib.safr_batch_get_status.argtypes = [vp]
     lib.safr_batch_launches.argtypes = [vp]
     lib.safr_batch_graph.argtypes = [vp]
+    lib.safr_batch_chains.argtypes = [vp]
     lib.safr_batch_destroy.argtypes = [vp]
     lib.safr_filter_train.argtypes = [vp, C.POINTER(safr_filter_config), C.POINTER(C.c_float),
                                       C.POINTER(safr_filter_result), vp]
@@ -413,6 +415,10 @@ def safr_batch_reconstruct(batch: int, wavefronts, layers, in_scales=None, out_s
 
 def safr_batch_get_status(batch: int) -> int:
     return load().safr_batch_get_status(batch)
+
+
+def safr_batch_chains(batch: int) -> int:
+    return load().safr_batch_chains(batch)
 
 
 def safr_batch_launches(batch: int) -> int:

@@ -31,11 +31,20 @@ def test_layers_do_not_depend_on_the_grid(oracle_mod):
         dt = torch.float64 if g.get("precision") == "fp64" else torch.float32
         tol = 1e-12 if g.get("precision") == "fp64" else 1e-5
         p = safr.Plan(g, device=0, path=safr.SAFR_PATH_FUSED)
-        for ctas in (0, nsm // 2, nsm // 4, 7):
+        xin = torch.from_numpy(x).to("cuda:0", dt)
+        first = None
+        # launches on one plan alternate grid sizes: each launch's grid barrier counts its own CTAs
+        for ctas in (0, nsm // 2, nsm // 4, 7, nsm // 2, 0):
             safr.safr_set_grid(p.handle, ctas)
             assert safr.safr_get_grid(p.handle) == (ctas or nsm)
-            got = p.reconstruct(torch.from_numpy(x).to("cuda:0", dt)).double().cpu().numpy()
+            out = p.reconstruct(xin)
+            got = out.double().cpu().numpy()
             assert _rel(got, ref) <= tol, (g["name"], ctas, _rel(got, ref))
+            if ctas == 0:
+                if first is None:
+                    first = out.clone()
+                else:
+                    assert torch.equal(out, first), g["name"]
         assert safr.safr_get_status(p.handle) == 0
         p.close()
 
