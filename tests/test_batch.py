@@ -129,3 +129,26 @@ def test_autotune_keeps_the_layers_and_caches_by_shape():
     assert (iq["path"], iq["tile_rows"], iq["autotuned"]) == (info["path"], info["tile_rows"], 1)
     p.close()
     q.close()
+
+
+@pytest.mark.gpu
+def test_batch_with_a_repeated_plan_stays_in_one_chain():
+    """Two frames on one plan share its workspaces, so the batch keeps them in one chain."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr, synth
+    dev = torch.device("cuda:0")
+    g = synth.scaled(synth.config(2), M=64, P=20)
+    p, q = safr.Plan(g, device=0), safr.Plan(g, device=0)
+    batch = safr.safr_batch_create([p.handle, q.handle, p.handle])
+    xs = [torch.from_numpy(synth.random_frame(g, 90 + i).astype(np.float32)).to(dev) for i in range(3)]
+    outs = [p.empty_layers() for _ in range(3)]
+    safr.safr_batch_reconstruct(batch, xs, outs)
+    torch.cuda.synchronize(dev)
+    assert safr.safr_batch_chains(batch) == 1
+    for plan, x, out in zip((p, q, p), xs, outs):
+        assert torch.equal(out, plan.reconstruct(x))
+    assert safr.safr_batch_get_status(batch) == 0
+    safr.safr_batch_destroy(batch)
+    p.close()
+    q.close()
