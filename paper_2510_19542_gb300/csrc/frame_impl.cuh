@@ -25,9 +25,12 @@
 //             frequency (Algorithm 1, line 5) straight into the registers of
 //             the inverse FFT along j -> w2[group][l][k][p];
 //   phase 3   (layer, tile of output rows): the needed rows of w2 staged in
-//             shared memory, one inverse transform per source row pair
-//             (complex-to-real, IDFT2 with 1/M^2), bilinear resample of LGS
-//             layers from pitch c_l*delta to delta, sum of the groups
+//             shared memory; for LGS layers the row half of the bilinear
+//             resample from pitch c_l*delta to delta is taken on the staged
+//             spectra (a real combination of two rows commutes with the
+//             transform along q), so every group needs one transform per
+//             output row pair; inverse transforms (complex-to-real, IDFT2 with
+//             1/M^2), the column half of the resample, sum of the groups
 //             (Algorithm 3, line 4), optional FP16 with a power-of-two scale
 //             from the layer energy (Parseval), store.
 //
@@ -66,7 +69,7 @@ struct Frame2Params {
     int ntask2;                // phase-2 (group, layer) tasks = ngroups * L
     int rt3, tiles3, n3;       // phase-3 rows per item, tiles per layer, items
     int st3[2];                // staged source rows per group (odd stride)
-    int cap3;                  // row-pair transforms of one phase-3 item (rows of Zr)
+    int cap3;                  // row-pair transforms of one phase-3 item (rows of Z)
     int nsrc3[2];              // max source rows per group and item
     int any_tt, any_resample;
     int stage_b;               // 1: B column block staged in shared memory by TMA
@@ -774,8 +777,8 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             const int first0 = rs0 ? ti0[p0] : p0;
             const int nsrc0 = rs0 ? ti0[p0 + nr - 1] + 2 - first0 : nr;
             const int nsrc1 = two ? nr : 0;  // the NGS group is never resampled
-            const int npair0 = (nsrc0 + 1) >> 1, npair1 = (nsrc1 + 1) >> 1;
-            const int ntot = npair0 + npair1;
+            const int npair = (nr + 1) >> 1;  // transforms per group: one per output row pair
+            const int ntot = two ? 2 * npair : npair;
             if (nsrc0 > fp.nsrc3[0] || nsrc1 > fp.nsrc3[1] || ntot > fp.cap3) {  // sized on the host; never expected
                 if (tid == 0) atomicExch(fp.status, (int)SAFR_ERR_DEVICE);
                 continue;
@@ -807,44 +810,79 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             }
             __syncthreads();
             SAFR_MARK(18, it == b);
-            // one inverse transform per source row pair: Z[k] = X1[k] + i X2[k] over the
-            // full length M from the stored half spectra, built directly in the permuted order
+            // one inverse transform per output row pair r = 2i, 2i + 1 of each group:
+            // Z[k] = X1[k] + i X2[k] over the full length M from the stored half spectra,
+            // built directly in the permuted order.  An LGS row's spectrum is the
+            // combination (1 - f) S[s] + f S[s + 1] of its two staged source rows.
             for (int u0 = 0; u0 < ntot; u0 += UNITS) {
                 const int task = u0 + unit;
                 const bool act = task < ntot;
                 if (!__any_sync(0xffffffffu, act)) continue;
                 const int tk = act ? task : 0;  // an idle slot reads row pair 0 of group 0 (always staged)
-                const bool g1 = tk >= npair0;
-                const int i = g1 ? tk - npair0 : tk;
+                const bool g1 = tk >= npair;
+                const int i = g1 ? tk - npair : tk;
                 const C *sg = g1 ? stg1 : stg0;
                 const int st = g1 ? st1 : st0;
-                const bool hasb = 2 * i + 1 < (g1 ? nsrc1 : nsrc0);
+                const bool hasb = 2 * i + 1 < nr;
                 // frequency k < M/2 reads stored column k; k > M/2 reads column M - k (conjugate
                 // symmetry); every lane loads from a valid address first, then selects
                 C v[RR];
-                const int ib = hasb ? 2 * i + 1 : 2 * i;
                 constexpr int RB = RR < 8 ? RR : 8;  // values loaded per batch (bounds the registers at large M)
+                if (!g1 && rs0) {  // warp-uniform: the LGS group's rows, resampled along p
+                    const int ra = p0 + 2 * i, rb = hasb ? ra + 1 : ra;
+                    const int sa = ti0[ra] - first0, sb = ti0[rb] - first0;
+                    const R fa = tfw[ra], fb = tfw[rb];
 #pragma unroll
-                for (int r0 = 0; r0 < RR; r0 += RB) {
-                    C x1[RB], x2[RB];
+                    for (int r0 = 0; r0 < RR; r0 += RB) {
+                        C x1[RB], y1[RB], x2[RB], y2[RB];
 #pragma unroll
-                    for (int u = 0; u < RB; ++u) {
-                        const int k = r0 + u + RR * bt;
-                        const int kk = k < Mh ? k : (k > Mh ? M - k : 0);
-                        const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
-                        x1[u] = row[2 * i];
-                        x2[u] = row[ib];
-                    }
-#pragma unroll
-                    for (int u = 0; u < RB; ++u) {
-                        const int k = r0 + u + RR * bt;
-                        C a = x1[u], c = hasb ? x2[u] : C{0, 0};
-                        if (k == 0) {
-                            a.y = 0;
-                            c.y = 0;
+                        for (int u = 0; u < RB; ++u) {
+                            const int k = r0 + u + RR * bt;
+                            const int kk = k < Mh ? k : (k > Mh ? M - k : 0);
+                            const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
+                            x1[u] = row[sa];
+                            y1[u] = row[sa + 1];
+                            x2[u] = row[sb];
+                            y2[u] = row[sb + 1];
                         }
-                        const C lo = C{a.x - c.y, a.y + c.x}, hi = C{a.x + c.y, c.x - a.y};
-                        v[r0 + u] = !act || k == Mh ? C{0, 0} : (k < Mh ? lo : hi);
+#pragma unroll
+                        for (int u = 0; u < RB; ++u) {
+                            const int k = r0 + u + RR * bt;
+                            C a = C{(R(1) - fa) * x1[u].x + fa * y1[u].x, (R(1) - fa) * x1[u].y + fa * y1[u].y};
+                            C c = hasb ? C{(R(1) - fb) * x2[u].x + fb * y2[u].x, (R(1) - fb) * x2[u].y + fb * y2[u].y}
+                                       : C{0, 0};
+                            if (k == 0) {
+                                a.y = 0;
+                                c.y = 0;
+                            }
+                            const C lo = C{a.x - c.y, a.y + c.x}, hi = C{a.x + c.y, c.x - a.y};
+                            v[r0 + u] = !act || k == Mh ? C{0, 0} : (k < Mh ? lo : hi);
+                        }
+                    }
+                } else {
+                    const int ib = hasb ? 2 * i + 1 : 2 * i;
+#pragma unroll
+                    for (int r0 = 0; r0 < RR; r0 += RB) {
+                        C x1[RB], x2[RB];
+#pragma unroll
+                        for (int u = 0; u < RB; ++u) {
+                            const int k = r0 + u + RR * bt;
+                            const int kk = k < Mh ? k : (k > Mh ? M - k : 0);
+                            const C *row = sg + kk * st + (((kk / RR) >> 1) & 15);
+                            x1[u] = row[2 * i];
+                            x2[u] = row[ib];
+                        }
+#pragma unroll
+                        for (int u = 0; u < RB; ++u) {
+                            const int k = r0 + u + RR * bt;
+                            C a = x1[u], c = hasb ? x2[u] : C{0, 0};
+                            if (k == 0) {
+                                a.y = 0;
+                                c.y = 0;
+                            }
+                            const C lo = C{a.x - c.y, a.y + c.x}, hi = C{a.x + c.y, c.x - a.y};
+                            v[r0 + u] = !act || k == Mh ? C{0, 0} : (k < Mh ? lo : hi);
+                        }
                     }
                 }
                 wfft_inv<M>(v, tw, t);
@@ -873,27 +911,24 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 inv_scale = (R)(1.0f / sc);
                 if (p0 == 0 && tid == 0) fp.out_scales[l] = sc;
             }
-            // source row s of group 0 is Z[s / 2] (real part for even s, imaginary for odd)
+            // output row r of a group is Z[r / 2] of that group (real part for even r, imaginary for odd)
             const R f = fp.inv_M2 * inv_scale;
             TOUT *outp = (TOUT *)fp.out + ((size_t)l * M + p0) * M;
             for (int idx = tid; idx < nr * M; idx += NTH) {
                 const int r = idx >> LOGM, q = idx & (M - 1);
+                const C *zr = Z + (size_t)(r >> 1) * M;
                 R v;
-                if (rs0) {  // bilinear in the LGS layer grid (pitch c_l delta)
-                    const R fu = tfw[p0 + r], fv = tfw[q];
+                if (rs0) {  // the column half of the bilinear resample (the row half was taken on the spectra)
+                    const R fv = tfw[q];
                     const int j0u = ti0[q];
                     const int ja = j0u & (M - 1), jb = (j0u + 1) & (M - 1);
-                    const int s0 = ti0[p0 + r] - first0, s1 = s0 + 1;
-                    const C *za = Z + (size_t)(s0 >> 1) * M, *zb = Z + (size_t)(s1 >> 1) * M;
-                    const R a0 = (s0 & 1) ? za[ja].y : za[ja].x, a1 = (s0 & 1) ? za[jb].y : za[jb].x;
-                    const R b0v = (s1 & 1) ? zb[ja].y : zb[ja].x, b1v = (s1 & 1) ? zb[jb].y : zb[jb].x;
-                    v = (R(1) - fu) * ((R(1) - fv) * a0 + fv * a1) + fu * ((R(1) - fv) * b0v + fv * b1v);
+                    const R a0 = (r & 1) ? zr[ja].y : zr[ja].x, a1 = (r & 1) ? zr[jb].y : zr[jb].x;
+                    v = (R(1) - fv) * a0 + fv * a1;
                 } else {
-                    const C zz = Z[(size_t)(r >> 1) * M + q];
-                    v = (r & 1) ? zz.y : zz.x;
+                    v = (r & 1) ? zr[q].y : zr[q].x;
                 }
                 if (two) {  // the NGS group's rows follow group 0's pairs
-                    const C zz = Z[(size_t)(npair0 + (r >> 1)) * M + q];
+                    const C zz = Z[(size_t)(npair + (r >> 1)) * M + q];
                     v += (r & 1) ? zz.y : zz.x;
                 }
                 R val = v * f;
@@ -1003,9 +1038,9 @@ struct Frame2Host {
                             mx = std::max(mx, bq + 2 - a);
                         }
                     }
-                nsm_[gi] = mx + (mx & 1);  // even: whole row pairs
+                nsm_[gi] = mx + (mx & 1);  // staged source rows
             }
-            const int cap3 = (nsm_[0] + nsm_[1]) / 2;  // row pairs of one item
+            const int cap3 = pl->ngroups * ((rt + 1) / 2);  // row-pair transforms of one item
             size_t s3 = rsb;
             for (int gi = 0; gi < pl->ngroups; ++gi) s3 += (size_t)Mh * odd_at_least(nsm_[gi] + 15) * cs;
             s3 += (size_t)cap3 * M * cs;
