@@ -7,17 +7,17 @@
 // all data in registers, lanes exchanged by shuffles.
 //
 //   prologue  per-lane twiddles and this CTA's later-phase tables are loaded
-//             into registers; B of every column after this CTA's first goes
-//             to L2 by bulk prefetch;
+//             into registers; the CTA's first B column block (all groups,
+//             layers and stars; contiguous) is copied into shared memory by
+//             TMA (cp.async.bulk) and lands during phase 1; B of every column
+//             after this CTA's first goes to L2 by bulk prefetch;
 //   phase 1   one transform per row pair of the zero-padded wavefronts
 //             (Section 2): rows a0, a0 + 1 packed as z = psi_a0 + i psi_a0+1,
 //             forward FFT along q, split into the two half spectra
 //             -> w1[g][k][p] (k < M/2).  LGS rows of a mixed plan also give
 //             their share of the two linear functionals that yield the tip and
 //             tilt of the least-squares plane over the pupil (Algorithm 3,
-//             line 3).  Once the frame data has landed, the CTA's first B
-//             column block (all groups, layers and stars; contiguous) is
-//             copied into shared memory by TMA (cp.async.bulk);
+//             line 3);
 //   phase 2   column k: one transform per star, FFT along p -> d_g(j, k);
 //             removeTT in the frequency domain, d_g -= b_g X(j,k) + c_g Y(j,k)
 //             with X, Y = DFT2 of x and y on the mask (DFT2 is linear); then
@@ -298,6 +298,37 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     const int t = lane & (LW - 1);                             // lane within the transform
     const int unit = warp * S::TPW + (lane >> LB);             // transform slot of this lane
     const int bt = LB > 0 ? (int)(__brev((unsigned)t) >> (32 - LB)) : 0;  // brev(t)
+    // first touches by warp 1, before anything else: the frame data of this CTA's phase-1 rows
+    // line by line into L2, and one line of each region it stores to or stages from later (its
+    // phase-2 columns of w1 and w2, its first phase-3 tile of w2 and of the layers).  The cold
+    // reads and address translations (the L2 was flushed, or the data is new) then overlap the
+    // prologue instead of sitting in front of the phases that need them.  Grids up to 256 only:
+    // at 512 the extra registers cost more than the early touches gain (measured).
+    if (M <= 256 && warp == 1) {
+        const void *pf = nullptr;
+        const int lo = (int)(((long long)b * fp.n1) / nb), hi = (int)(((long long)(b + 1) * fp.n1) / nb);
+        if (lane < 24) {
+            if (lo < hi) {
+                const int g0 = lo / fp.npr, g1 = (hi - 1) / fp.npr;
+                const size_t r0 = (size_t)g0 * P + 2 * (lo - g0 * fp.npr);
+                const size_t r1 = (size_t)g1 * P + min(2 * (hi - 1 - g1 * fp.npr) + 1, P - 1) + 1;
+                const size_t off = (size_t)lane * 128, beg = r0 * P * sizeof(TIN), end = r1 * P * sizeof(TIN);
+                if (beg + off < end) pf = (const char *)fp.in + beg + off;
+            }
+        } else if (lane == 24) {
+            if (fp.any_tt && lo < hi) pf = fp.mask_bits + (size_t)(2 * (lo - (lo / fp.npr) * fp.npr)) * fp.mask_words;
+        } else if (lane == 25 || lane == 26) {
+            if (b < Mh) pf = fp.w1 + ((size_t)(lane == 25 ? 0 : G - 1) * Mh + b) * P;
+        } else if (lane == 27 || lane == 28) {
+            if (b < Mh) pf = fp.w2 + ((size_t)(lane == 27 ? 0 : fp.ngroups * L - 1) * Mh + b) * M;
+        } else if (b < fp.n3) {
+            const int l = b / fp.tiles3, p0 = (b - l * fp.tiles3) * fp.rt3;
+            if (lane == 29) pf = (const char *)fp.out + ((size_t)l * M + p0) * M * sizeof(TOUT);
+            else if (lane == 30) pf = fp.w2 + (size_t)l * (M / 2) * M;
+            else if (fp.ngroups > 1) pf = fp.w2 + ((size_t)L + l) * (M / 2) * M;
+        }
+        if (pf) prefetch_line(pf);
+    }
     // parameter copies by warps 2 and 3 (warp 0 issues the table copies first)
     if (warp == 2) {
 #pragma unroll
@@ -373,6 +404,10 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             tma_load_1d(ti0, fp.rs_i0 + (size_t)l * M, ib, &mbar_t);
             tma_load_1d(tfw, fp.rs_w + (size_t)l * M, wb, &mbar_t);
         }
+        // this CTA's first B column block: it lands during phase 1, so phase 1's stores and the
+        // first grid barrier do not queue behind the 21 MB stream (issued after the frame data
+        // had landed instead, it held the first barrier back by about 1 us)
+        if (fp.stage_b && b < Mh) copy_b(b);
     }
     // every thread waits for the tables before its first transform (no thread leaves
     // on a timeout here: the status word records it and the barriers stay balanced)
@@ -391,6 +426,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     __syncthreads();  // the parameter copies
     SAFR_MARK(1, true);
 
+    tma_pending = fp.stage_b && b < Mh;  // the B block copy issued above
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
     auto drain = [&]() {
         if (tma_pending) mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status);
@@ -404,6 +440,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         polc_phase<M, R, TIN, TOUT>(fp, G, L, P, b, nb);
         if (!grid_sync_bounded(fp.bar, bar_next, fp.status, fp.timeout_ns, &bar_flag, nullptr)) {
             mbar_wait_bounded(&mbar_t, tph, fp.timeout_ns, fp.status);  // the table copies are not left in flight
+            drain();                                                     // nor the B block copy
             return false;
         }
         bar_next += nb;
@@ -529,8 +566,6 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 }
             }
             SAFR_MARK(2, first);
-            // the frame data has landed: B streams in behind it
-            if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);
             SAFR_MARK(3, first);
             if (first) tables();
             wfft_fwd<M>(v, tw, t);
@@ -556,8 +591,6 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             }
             first = false;
         }
-        if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);  // a CTA without phase-1 rows
-        if (fp.stage_b && b < Mh) tma_pending = true;
         if (first) tables();  // a warp without phase-1 rows
     }
     if (b == fp.skip_cta) {  // test hook: every other CTA's first barrier must time out
