@@ -267,6 +267,18 @@ int safr_get_grid(safr_plan_t plan);
 int safr_get_path(safr_plan_t plan);
 
 /*
+ * Output rows per phase-3 item of the persistent kernel (the paper fixes no
+ * tiling): 0 (the default) lets the cost model choose; an even value from 2
+ * to min(32, M) forces it (safr_autotune sets it the same way).  The layers
+ * depend on it only through rounding: rows are paired into complex
+ * transforms from the top of each tile.  SAFR_ERR_INVALID_ARG for any other
+ * value; SAFR_ERR_UNSUPPORTED_SIZE (choice unchanged) when the plan has no
+ * persistent kernel or the tile does not fit in shared memory.
+ * safr_get_plan_info reports the height in use (tile_rows).
+ */
+safr_status safr_set_tile_rows(safr_plan_t plan, int rows);
+
+/*
  * Test hook for the bounded grid barrier of SAFR_PATH_FUSED: with cta >= 0,
  * that CTA leaves the next frames before the first barrier, so every other
  * CTA's wait runs out after timeout_s seconds and the kernel records

@@ -730,6 +730,23 @@ safr_status safr_set_grid(safr_plan_t plan, int ctas)
 
 int safr_get_grid(safr_plan_t plan) { return plan ? plan->f2_grid : 0; }
 
+safr_status safr_set_tile_rows(safr_plan_t plan, int rows)
+{
+    if (!plan || rows < 0 || (rows & 1) || rows > std::min(32, plan->M)) return SAFR_ERR_INVALID_ARG;
+    if (!plan->fused_ok) return SAFR_ERR_UNSUPPORTED_SIZE;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return SAFR_ERR_CUDA;
+    const int old = plan->f2_rt_force;
+    plan->f2_rt_force = rows;
+    if (!safr::configure_fused(plan)) {  // the tile does not fit: keep the previous choice
+        plan->f2_rt_force = old;
+        safr::configure_fused(plan);
+        return SAFR_ERR_UNSUPPORTED_SIZE;
+    }
+    plan->traced = 0;
+    return SAFR_OK;
+}
+
 int safr_get_path(safr_plan_t plan)
 {
     if (!plan) return -1;

@@ -41,7 +41,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
             "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
             "safr_plan_save", "safr_plan_load", "safr_trace_stamps", "safr_set_grid", "safr_get_grid",
-            "safr_batch_chains"]
+            "safr_batch_chains", "safr_set_tile_rows"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
     lib.safr_get_path.argtypes = [vp]
     lib.safr_set_grid.argtypes = [vp, C.c_int]
     lib.safr_get_grid.argtypes = [vp]
+    lib.safr_set_tile_rows.argtypes = [vp, C.c_int]
     lib.safr_debug_skip_barrier.argtypes = [vp, C.c_int, C.c_double]
     lib.safr_destroy.argtypes = [vp]
     lib.safr_reconstruct_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, vp]
@@ -282,6 +283,11 @@ def safr_set_grid(plan: int, ctas: int):
 
 def safr_get_grid(plan: int) -> int:
     return load().safr_get_grid(plan)
+
+
+def safr_set_tile_rows(plan: int, rows: int):
+    """Output rows per phase-3 item of the persistent kernel (0: the cost model's choice)."""
+    _check(load().safr_set_tile_rows(plan, int(rows)), "safr_set_tile_rows")
 
 
 def safr_trace_stamps(plan: int) -> np.ndarray:
