@@ -118,6 +118,19 @@ __device__ __forceinline__ unsigned long long gtimer()
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// One element global -> shared without registers (cp.async; 8 bytes through L1, 16 bytes around it).
+// The copies of a thread complete at cp_async_wait_all.
+template <typename C>
+__device__ __forceinline__ void cp_async_el(C *dst, const C *src)
+{
+    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "complex float or double");
+    if constexpr (sizeof(C) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // a complex value from shared memory at byte address a (shared window)
 template <typename C>
 __device__ __forceinline__ C lds_c(unsigned a);
@@ -817,29 +830,23 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 continue;
             }
             // stage the needed rows of every column, one warp per column k:
-            // stg0[k][s] = w2[0][l][k][first0 + s], stg1[k][s] = w2[1][l][k][p0 + s]
+            // stg0[k][s] = w2[0][l][k][first0 + s], stg1[k][s] = w2[1][l][k][p0 + s],
+            // as asynchronous copies: all of a lane's copies are in flight at once
             {
                 const C *src0 = fp.w2 + (size_t)l * Mh * M;
                 const C *src1 = fp.w2 + ((size_t)L + l) * Mh * M;
                 constexpr int KW = (Mh + NW - 1) / NW;  // columns per warp
-                constexpr int KB = KW < 8 ? KW : 8;     // of which in flight at once
-                for (int s = lane; s < nsrc0 || s < nsrc1; s += 32)
-                    for (int t0 = 0; t0 < KW; t0 += KB) {
-                        C v0[KB], v1[KB];
-#pragma unroll
-                        for (int u = 0; u < KB; ++u) {
-                            const int k = warp + NW * (t0 + u);
-                            if (k < Mh && s < nsrc0) v0[u] = __ldcg(src0 + ((size_t)k << LOGM) + ((first0 + s) & (M - 1)));
-                            if (k < Mh && s < nsrc1) v1[u] = __ldcg(src1 + ((size_t)k << LOGM) + p0 + s);
-                        }
-#pragma unroll
-                        for (int u = 0; u < KB; ++u) {
-                            const int k = warp + NW * (t0 + u);
-                            const int sk = ((k / RR) >> 1) & 15;
-                            if (k < Mh && s < nsrc0) stg0[k * st0 + sk + s] = v0[u];
-                            if (k < Mh && s < nsrc1) stg1[k * st1 + sk + s] = v1[u];
-                        }
+                for (int s = lane; s < nsrc0 || s < nsrc1; s += 32) {
+#pragma unroll 4
+                    for (int u = 0; u < KW; ++u) {
+                        const int k = warp + NW * u;
+                        const int sk = ((k / RR) >> 1) & 15;
+                        if (k < Mh && s < nsrc0)
+                            cp_async_el(stg0 + k * st0 + sk + s, src0 + ((size_t)k << LOGM) + ((first0 + s) & (M - 1)));
+                        if (k < Mh && s < nsrc1) cp_async_el(stg1 + k * st1 + sk + s, src1 + ((size_t)k << LOGM) + p0 + s);
                     }
+                }
+                cp_async_wait_all();
             }
             __syncthreads();
             SAFR_MARK(18, it == b);
