@@ -33,12 +33,6 @@ inline bool smem_limit_allows(const void *kernel, size_t need)
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-// Prefetch of the line holding p into L2 (also resolves its address translation).
-__device__ __forceinline__ void prefetch_line(const void *p)
-{
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(p) : "memory");
-}
-
 // Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
 {
