@@ -242,8 +242,10 @@ __device__ __forceinline__ bool grid_sync_bounded(unsigned long long *bar, unsig
 __host__ __device__ constexpr int frame2_threads(int) { return 512; }
 
 // Phase 0 of an AO loop step: psi~_g = mask (psi_g + sum_l a_l(sample point)), bilinear in the
-// state a = out, one sample per thread over the whole grid (the sample table is described in
-// loop.cu).  Not inlined: its registers stay out of the frame's own allocation.
+// state a = out (the sample table is described in loop.cu).  A CTA computes exactly the rows that
+// its own phase 1 transforms (the same row pairs, contiguous in the [G][P] row space), one sample
+// per thread, so a block barrier orders phase 0 before phase 1 and no grid barrier is needed.
+// Not inlined: its registers stay out of the frame's own allocation.
 template <int M, typename R, typename TIN, typename TOUT>
 __device__ __noinline__ void polc_phase(const Frame2Params<R> &fp, int G, int L, int P, int b, int nb)
 {
@@ -255,7 +257,12 @@ __device__ __noinline__ void polc_phase(const Frame2Params<R> &fp, int G, int L,
     const TOUT *aa = (const TOUT *)fp.out;
     TIN *dst = (TIN *)fp.in;
     const int nth = blockDim.x;
-    for (long idx = (long)b * nth + threadIdx.x; idx < (long)G * P * P; idx += (long)nb * nth) {
+    const int lo = (int)(((long long)b * fp.n1) / nb), hi = (int)(((long long)(b + 1) * fp.n1) / nb);
+    if (lo >= hi) return;
+    const int g0 = lo / fp.npr, g1 = (hi - 1) / fp.npr;
+    const long r0 = (long)g0 * P + 2 * (lo - g0 * fp.npr);                            // first row
+    const long r1 = (long)g1 * P + min(2 * (hi - 1 - g1 * fp.npr) + 1, P - 1) + 1;    // past the last
+    for (long idx = r0 * P + threadIdx.x; idx < r1 * P; idx += nth) {
         const int g = (int)(idx / ((long)P * P)), pq = (int)(idx % ((long)P * P)), p = pq / P, q = pq % P;
         R acc = 0;
         if (pmask[pq]) {
@@ -420,12 +427,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     // sample per thread over the whole grid; the samples' table is described in loop.cu
     if (fp.polc_tab) {
         polc_phase<M, R, TIN, TOUT>(fp, G, L, P, b, nb);
-        if (!grid_sync_bounded(fp.bar, bar_next, fp.status, fp.timeout_ns, &bar_flag, nullptr)) {
-            mbar_wait_bounded(&mbar_t, tph, fp.timeout_ns, fp.status);  // the table copies are not left in flight
-            drain();                                                     // nor the B block copy
-            return false;
-        }
-        bar_next += nb;
+        __syncthreads();  // the samples of this CTA's phase-1 rows, written by its own threads
     }
 
     // ---- phase 1: row pairs ----------------------------------------------------
@@ -1000,7 +1002,7 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     const unsigned long long base = bar_count_read(fp.bar);
     unsigned bph = 0;
     if (frame_body<M, R, TIN, TOUT, CK>(fp, base, bph, 0u, true))
-        bar_count_advance(fp.bar, base, (fp.polc_tab ? 3ull : 2ull) * gridDim.x);
+        bar_count_advance(fp.bar, base, 2ull * gridDim.x);
 }
 
 // ----------------------------------------------------------------------------

@@ -234,8 +234,9 @@ safr_status safr_loop_step(safr_plan_t plan, const void *d_wavefronts, void *d_a
     LoopDeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
     if (safr::use_fused(plan)) {
-        // one launch: the persistent kernel computes the POLC data into the staging buffer (phase 0,
-        // one more grid barrier), reconstructs, and blends its layers into the state as it stores them
+        // one launch: the persistent kernel computes the POLC data into the staging buffer (phase 0:
+        // each CTA the rows of its own phase 1), reconstructs, and blends its layers into the state
+        // as it stores them
         plan->loop_blend = 1;
         plan->loop_gain = gain;
         plan->loop_polc_psi = d_wavefronts;
