@@ -124,10 +124,11 @@ def test_tiny_ngs_fp32(safr, synth, oracle_mod, path):
 
 
 @pytest.mark.parametrize("M,P,L", [(64, 20, None), (128, 40, None), (64, 37, 5), (32, 9, 3), (8, 8, 2),
-                                   (16, 5, 9), (256, 80, 12)])
+                                   (16, 5, 9), (256, 80, 12), (512, 160, 6)])
 def test_mixed_lgs_ngs_fp32(safr, synth, oracle_mod, M, P, L, path):
     """Split tomography with removeTT and the metric resample; odd P gives a
-    ragged last row pair and an odd pad offset."""
+    ragged last row pair and an odd pad offset.  The 512 grid runs the
+    transforms with 16 values per lane (loaded 8 at a time) and B unstaged."""
     g = synth.scaled(synth.config(2), M=M, P=P, L=L)
     check(safr, oracle_mod, g, synth.frame(g), path=path)
 

@@ -30,7 +30,8 @@ def _cases(synth):
     small = synth.scaled(synth.config(2), M=64, P=20)
     small64 = dict(synth.scaled(synth.config(2), M=32, P=10), precision="fp64")
     small64["name"] += "-fp64"
-    return [small, small64, synth.config(2)]
+    big = synth.scaled(synth.config(2), M=512, P=160, L=6)  # 16 values per lane, B not staged
+    return [small, small64, synth.config(2), big]
 
 
 @pytest.mark.gpu
