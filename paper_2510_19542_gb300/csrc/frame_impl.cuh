@@ -799,6 +799,10 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
         C *stg1 = stg0 + (size_t)Mh * st0;                      // [Mh][st1]
         C *Z = stg1 + (size_t)Mh * st1;                         // [cap3][M] inverse row transforms
         const bool two = fp.ngroups > 1;
+        constexpr int KW = (Mh + NW - 1) / NW;  // staged columns per warp
+        // M >= 512 without a resample: an item's staging copies are issued while the previous
+        // item stores (the staging buffers are free once its transforms are done)
+        bool staged_ahead = false;
         for (int it = b; it < fp.n3; it += nb) {
             const int l = it / fp.tiles3, p0 = (it - l * fp.tiles3) * RT;
             const int nr = min(RT, M - p0);
@@ -818,15 +822,16 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             const int ntot = two ? 2 * npair : npair;
             if (nsrc0 > fp.nsrc3[0] || nsrc1 > fp.nsrc3[1] || ntot > fp.cap3) {  // sized on the host; never expected
                 if (tid == 0) atomicExch(fp.status, (int)SAFR_ERR_DEVICE);
+                cp_async_wait_all();
+                staged_ahead = false;
                 continue;
             }
             // stage the needed rows of every column, one warp per column k:
             // stg0[k][s] = w2[0][l][k][first0 + s], stg1[k][s] = w2[1][l][k][p0 + s],
             // as asynchronous copies: all of a lane's copies are in flight at once
-            {
+            if (M < 512 || !staged_ahead) {
                 const C *src0 = fp.w2 + (size_t)l * Mh * M;
                 const C *src1 = fp.w2 + ((size_t)L + l) * Mh * M;
-                constexpr int KW = (Mh + NW - 1) / NW;  // columns per warp
                 for (int s = lane; s < nsrc0 || s < nsrc1; s += 32) {
 #pragma unroll 4
                     for (int u = 0; u < KW; ++u) {
@@ -837,8 +842,8 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                         if (k < Mh && s < nsrc1) cp_async_el(stg1 + k * st1 + sk + s, src1 + ((size_t)k << LOGM) + p0 + s);
                     }
                 }
-                cp_async_wait_all();
             }
+            cp_async_wait_all();
             __syncthreads();
             SAFR_MARK(18, it == b);
             // one inverse transform per output row pair r = 2i, 2i + 1 of each group:
@@ -924,6 +929,26 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             SAFR_MARK(19, it == b);
             __syncthreads();
             SAFR_MARK(20, it == b);
+            if constexpr (M >= 512) {  // the next item's rows, while this one stores (no resample: rows p0..)
+                staged_ahead = false;
+                const int itn = it + nb;
+                if (!rs0 && itn < fp.n3) {
+                    const int ln = itn / fp.tiles3, p0n = (itn - ln * fp.tiles3) * RT, nrn = min(RT, M - p0n);
+                    const int ns1 = two ? nrn : 0;
+                    const C *src0 = fp.w2 + (size_t)ln * Mh * M;
+                    const C *src1 = fp.w2 + ((size_t)L + ln) * Mh * M;
+                    for (int s = lane; s < nrn || s < ns1; s += 32) {
+#pragma unroll 4
+                        for (int u = 0; u < KW; ++u) {
+                            const int k = warp + NW * u;
+                            const int sk = ((k / RR) >> 1) & 15;
+                            if (k < Mh && s < nrn) cp_async_el(stg0 + k * st0 + sk + s, src0 + ((size_t)k << LOGM) + p0n + s);
+                            if (k < Mh && s < ns1) cp_async_el(stg1 + k * st1 + sk + s, src1 + ((size_t)k << LOGM) + p0n + s);
+                        }
+                    }
+                    staged_ahead = true;
+                }
+            }
             R inv_scale = R(1);
             if constexpr (std::is_same<TOUT, __half>::value) {
                 // layer energy sum_n |b(n)|^2 over the groups (fixed order) -> RMS = sqrt(energy) / M^2;
