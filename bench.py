@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--path", default="auto", choices=["auto", "fused", "passes"])
     ap.add_argument("--no-workloads", action="store_true", help="skip the secondary workloads (32-grid, 512-grid, batched, learned filter, loop step, refresh)")
+    ap.add_argument("--workloads", default="all",
+                    help="comma-separated secondary workloads to run (tiny, fp16-512, batch, learned, loop, refresh), "
+                         "or 'all'")
     return ap.parse_args()
 
 
@@ -651,18 +654,25 @@ def run_safr(args):
                 hbm_pk = float(json.load(f).get("hbm_gbs", 6800.0))
         except (OSError, ValueError):
             pass
-        for kk in (1, 3):
-            name, res = measure_workload(safr, synth, torch, dev, stream, kk, min(args.steps, 100), 5, flush_l2,
-                                         hbm_pk)
+        want = set(args.workloads.split(",")) if args.workloads != "all" else \
+            {"tiny", "fp16-512", "batch", "learned", "loop", "refresh"}
+        for kk, key in ((1, "tiny"), (3, "fp16-512")):
+            if key in want:
+                name, res = measure_workload(safr, synth, torch, dev, stream, kk, min(args.steps, 100), 5, flush_l2,
+                                             hbm_pk)
+                workloads[name] = res
+        if "batch" in want:
+            name, res = measure_batch(safr, synth, torch, dev, stream, min(args.steps, 20), 3, flush_l2, hbm_pk)
             workloads[name] = res
-        name, res = measure_batch(safr, synth, torch, dev, stream, min(args.steps, 20), 3, flush_l2, hbm_pk)
-        workloads[name] = res
-        name, res = measure_learned(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2)
-        workloads[name] = res
-        name, res = measure_loop(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2, hbm_pk)
-        workloads[name] = res
-        name, res = measure_refresh(safr, synth, torch, dev, stream, 10)
-        workloads[name] = res
+        if "learned" in want:
+            name, res = measure_learned(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2)
+            workloads[name] = res
+        if "loop" in want:
+            name, res = measure_loop(safr, synth, torch, dev, stream, min(args.steps, 100), 5, flush_l2, hbm_pk)
+            workloads[name] = res
+        if "refresh" in want:
+            name, res = measure_refresh(safr, synth, torch, dev, stream, 10)
+            workloads[name] = res
 
     if rank == 0:
         ph = np.array(phases)  # [steps][launches]
