@@ -22,7 +22,7 @@
 // counter-based generator (Philox4x32-10, Salmon et al., SC 2011); the loss
 // is the relative squared error of the reconstructed layer spectra (Parseval:
 // the squared error of the layers); its gradient flows through the MLP;
-// Adam updates FP32 master weights.  Held-out frames judge the learned filter
+// Adam updates FP32 master weights.  Held-out frames compare the learned filter
 // against plain SAFR, which stays in the plan if it is not beaten.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
