@@ -382,7 +382,7 @@ int safr_batch_launches(safr_batch_t batch);
 int safr_batch_graph(safr_batch_t batch);
 /* Concurrent chains of the batch's graph: frames of grids up to 256 on the
  * persistent kernel may run K at a time, each on 1/K of the SMs, with the
- * larger frames first on the whole GPU.  K in {1, 2, 4} is chosen at the
+ * larger frames first on the whole GPU.  K in {1, 2, 4, 8} is chosen at the
  * first capture by timing each graph (that call replays the batch a few times
  * on its own stream and synchronises); the layers do not depend on K.
  * Returns 0 before the first call. */

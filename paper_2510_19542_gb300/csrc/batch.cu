@@ -6,7 +6,7 @@
 // each call replays it with a single graph launch.  The graph bakes in the
 // frames' buffer pointers, so a call with other pointers captures it again.
 // Frames of grids up to 256 may run on K concurrent chains of the graph, each
-// on 1/K of the SMs; K in {1, 2, 4} is timed at the first capture.
+// on 1/K of the SMs; K in {1, 2, 4, 8} is timed at the first capture.
 //
 // A single persistent launch that loops over a device array of frame
 // parameters was built and measured slower than this graph (4.49 ms against
@@ -219,7 +219,7 @@ float time_graph(safr_batch_s *b, cudaGraphExec_t ex)
     return t[0] < 0 ? -1.0f : t[1];
 }
 
-// (Re)capture the batch's graph.  The first time, every chain count K in {1, 2, 4} that the batch
+// (Re)capture the batch's graph.  The first time, every chain count K in {1, 2, 4, 8} that the batch
 // can use is captured and timed, and the fastest is kept for later captures.
 void capture(safr_batch_s *b, const void *const *in, const float *const *isc, void *const *out, float *const *osc)
 {
@@ -227,9 +227,9 @@ void capture(safr_batch_s *b, const void *const *in, const float *const *isc, vo
     b->exec = nullptr;
     b->graph_failed = true;
     const int nconc = concurrent_count(b);
-    if (b->side.empty() && nconc >= 2) {  // streams and events of up to 4 chains
-        b->side.assign(3, nullptr);
-        b->ev.assign(4, nullptr);
+    if (b->side.empty() && nconc >= 2) {  // streams and events of up to 8 chains
+        b->side.assign(7, nullptr);
+        b->ev.assign(8, nullptr);
         bool ok = true;
         for (auto &st : b->side) ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
         for (auto &e : b->ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
@@ -243,7 +243,7 @@ void capture(safr_batch_s *b, const void *const *in, const float *const *isc, vo
         int best_k = 1;
         float best_t = -1.0f;
         cudaGraphExec_t best = nullptr;
-        for (int K : {1, 2, 4}) {
+        for (int K : {1, 2, 4, 8}) {
             if (K > 1 && nconc < K) continue;
             cudaGraphExec_t ex = nullptr;
             if (!capture_k(b, K, in, isc, out, osc, &ex)) continue;
