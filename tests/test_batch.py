@@ -7,6 +7,7 @@ layers agree with the untuned plan to FP32 rounding.
 """
 import numpy as np
 import pytest
+from layer_errors import assert_layers
 
 torch = pytest.importorskip("torch")
 
@@ -101,7 +102,7 @@ def test_batch_frame_against_oracle(oracle_mod):
     for g, x, out in zip(geoms, xs_np, outs):
         ref = oracle_mod.OraclePlan(g).reconstruct(x)
         got = out.double().cpu().numpy()
-        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5, g["name"]
+        assert_layers(got, ref, 1e-5, g["name"])
     safr.safr_batch_destroy(batch)
     for p in plans:
         p.close()

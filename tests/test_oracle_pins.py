@@ -372,3 +372,49 @@ def test_oracle_regression_values(oracle_mod):
     idx = np.array(gold["sample_lpq"])
     np.testing.assert_allclose(out[idx[:, 0], idx[:, 1], idx[:, 2]], gold["sample_values"],
                                rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Sampled reconstruction (the full-size point checks) against the full one
+# --------------------------------------------------------------------------
+def _sample_plans(M):
+    from paper_2510_19542_gb300 import synth
+    mixed = synth.scaled(synth.config(2), M=M, P=max(4, (5 * M) // 16 + 1), L=4)   # odd P: odd pad offset
+    lgs_metric = dict(mixed, kind=np.ones(9, np.int32), name=f"lgs-metric-{M}")
+    lgs_native = dict(lgs_metric, output_metric=0, name=f"lgs-native-{M}")
+    ngs = synth.scaled(synth.config(1), M=M, P=M // 2, L=3)
+    ngs["precision"] = "fp32"
+    return mixed, lgs_metric, lgs_native, ngs
+
+
+@pytest.mark.parametrize("M", [16, 32, 64])
+def test_samples_equal_full_reconstruction(oracle_mod, M):
+    """oracle_plan_reconstruct_samples (an IDFT2 sum at each point plus its own
+    bilinear indexing) equals oracle_plan_reconstruct (the whole IDFT2 of
+    Algorithm 1 and the separate resample, Section 3.2 / 3.3) at every sampled
+    (l, p, q).  The points cover the whole grid at M <= 32 and, at M = 64, the
+    rows and columns of the wrap seam (0, 1, M-2, M-1), the centre row M/2
+    (integer source position for every c_l) and random points; the ground
+    layer (c = 1) and the NGS group sample integer source positions, the
+    upper LGS layers of the metric plans wrap around the periodic grid."""
+    from paper_2510_19542_gb300 import synth
+    rng = np.random.default_rng(M)
+    for g in _sample_plans(M):
+        orc = oracle_mod.OraclePlan(g)
+        x = synth.random_frame(g, 17 + M)
+        full = orc.reconstruct(x)
+        L = full.shape[0]
+        if M <= 32:
+            l, p, q = np.meshgrid(np.arange(L), np.arange(M), np.arange(M), indexing="ij")
+            lpq = np.stack([l.ravel(), p.ravel(), q.ravel()], 1)
+        else:
+            edge = np.array([0, 1, M // 2, M - 2, M - 1])
+            pts = [(l, p, q) for l in range(L) for p in edge for q in range(M)]
+            pts += [(l, p, q) for l in range(L) for p in range(M) for q in edge]
+            pts += [tuple(v) for v in np.stack([rng.integers(0, L, 400), rng.integers(0, M, 400),
+                                                rng.integers(0, M, 400)], 1)]
+            lpq = np.array(pts)
+        got = orc.reconstruct_samples(x, lpq)
+        ref = full[lpq[:, 0], lpq[:, 1], lpq[:, 2]]
+        scale = np.abs(full).max()
+        assert np.abs(got - ref).max() <= 1e-12 * scale, (g["name"], np.abs(got - ref).max() / scale)

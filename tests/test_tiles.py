@@ -9,8 +9,8 @@ row pairings and odd final pairs.  The layers must match the FP64 oracle at
 the precision's tolerance for every height, and returning to the cost
 model's choice must give back the first result bit for bit.
 """
-import numpy as np
 import pytest
+from layer_errors import assert_layers
 
 torch = pytest.importorskip("torch")
 
@@ -20,10 +20,6 @@ def test_set_tile_rows_rejects_bad_arguments_without_a_gpu():
     lib = safr.load()
     for rows in (0, 2, 3, -2):
         assert lib.safr_set_tile_rows(None, rows) == safr.SAFR_ERR_INVALID_ARG
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def _cases(synth):
@@ -59,8 +55,7 @@ def test_every_tile_height_matches_the_oracle(oracle_mod):
             assert safr.safr_get_plan_info(p.handle)["tile_rows"] == rows
             got = p.reconstruct(xin).double().cpu().numpy()
             assert safr.safr_get_status(p.handle) == 0, (g["name"], rows)
-            err = _rel(got, ref)
-            assert err <= tol, (g["name"], rows, err)
+            assert_layers(got, ref, tol, (g["name"], rows))
             ran.append(rows)
         # heights with a ragged last tile and the cost model's own height were among them
         assert default_rows in ran and any(M % r for r in ran), (g["name"], ran)
