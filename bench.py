@@ -576,38 +576,51 @@ def job_throughput(world: int, steps: int, total_ms_max: float) -> float:
 # ----------------------------------------------------------------------------
 def measure_l2_bandwidth(torch, dev, stream):
     """L2 bandwidth from a plain device copy whose source and destination stay in
-    the L2 (best of a few sizes well below its 126 MB), read + write bytes over
-    the CUDA-event time of back-to-back copies."""
+    the L2 (sizes well below its 126 MB): 40 copies captured in one CUDA graph
+    (so that launch gaps do not count), read + write bytes over the CUDA-event
+    time of a replay; the best over a few sizes."""
     best, rows = 0.0, []
-    for mb in (8, 16, 24):
+    for mb in (8, 16, 24, 32):
         n = (mb << 20) // 4
         a = torch.ones(n, dtype=torch.float32, device=dev)
         b = torch.empty_like(a)
-        for _ in range(10):
-            b.copy_(a)
-        reps = 200
-        s = torch.cuda.Event(enable_timing=True)
-        e = torch.cuda.Event(enable_timing=True)
-        s.record(stream)
-        for _ in range(reps):
-            b.copy_(a)
-        e.record(stream)
-        e.synchronize()
-        gbs = 2.0 * n * 4 * reps / (s.elapsed_time(e) * 1e-3) / 1e9
+        reps = 40
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                b.copy_(a)
+        stream.wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(reps):
+                b.copy_(a)
+        times = []
+        for _ in range(5):
+            s = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            g.replay()
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+        gbs = 2.0 * n * 4 * reps / (min(times) * 1e-3) / 1e9
         rows.append({"mb_each": mb, "gbs": gbs})
         best = max(best, gbs)
-        del a, b
+        del g, a, b
     return best, rows
 
 
-def back_to_back(safr, torch, stream, plans, xs, outs, n):
+def back_to_back(safr, torch, stream, plans, xs, outs, n, host_us=30.0):
     """n frames submitted back to back (no host synchronisation between them),
     cycling over the given plans and frames; CUDA events bracket the whole run.
-    A bounded GPU sleep queued first lets the host run ahead of the GPU, so the
-    GPU never waits for a submission.  Returns (ms on the device, host seconds
-    spent submitting)."""
+    A bounded GPU sleep queued first, 1.5 x the expected host submission time
+    (host_us per frame), lets the host queue the frames before the GPU reaches
+    them, so the GPU does not wait for submissions.  Returns (ms on the device,
+    host seconds spent submitting, seconds of sleep queued)."""
     torch.cuda.synchronize()
-    torch.cuda._sleep(int(min(100e6, 30e3 * n)))  # about 15 us of GPU clock per frame, at most 50 ms
+    sleep_s = min(0.5, 1.5 * n * host_us * 1e-6)
+    torch.cuda._sleep(int(sleep_s * 2.07e9))  # GPU clock cycles (2070 MHz maximum SM clock)
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     s.record(stream)
@@ -619,7 +632,7 @@ def back_to_back(safr, torch, stream, plans, xs, outs, n):
     host_s = time.perf_counter() - t0
     e.record(stream)
     e.synchronize()
-    return s.elapsed_time(e), host_s
+    return s.elapsed_time(e), host_s, sleep_s
 
 
 def latency_run(safr, torch, stream, plan, xs, out, n, flush_l2, chunk=500):
@@ -710,7 +723,8 @@ def run_safr(args):
     # warm-up: every plan of the pool, back to back and flushed
     for i in range(args.warmup):
         one(i, False)
-    back_to_back(safr, torch, stream, pool, frames, outs, max(args.warmup, 1) * len(pool))
+    _, h_s, _ = back_to_back(safr, torch, stream, pool, frames, outs, max(args.warmup, 4) * len(pool))
+    host_us = 1e6 * h_s / (max(args.warmup, 4) * len(pool))  # host time per submitted frame
     torch.cuda.synchronize(dev)
     if world > 1:
         dist.barrier()
@@ -719,13 +733,14 @@ def run_safr(args):
     torch.cuda.synchronize(dev)
     wall0 = time.perf_counter()
     # (1) the value: frames submitted back to back over the pool (every B from HBM)
-    cold_ms, cold_host_s = back_to_back(safr, torch, stream, pool, frames, outs, args.steps)
+    cold_ms, cold_host_s, cold_sleep_s = back_to_back(safr, torch, stream, pool, frames, outs, args.steps, host_us)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
     # (2) the same frames back to back on one plan: B stays in the L2 (warm)
-    warm_ms, warm_host_s = back_to_back(safr, torch, stream, [plan], frames, [layers], args.steps)
+    warm_ms, warm_host_s, warm_sleep_s = back_to_back(safr, torch, stream, [plan], frames, [layers], args.steps,
+                                                      host_us)
     # (3) per-frame latency, L2 flushed before every frame
     lat = latency_run(safr, torch, stream, plan, frames, layers, args.latency_frames, flush_l2)
     clk = clocks.stop()
@@ -839,10 +854,12 @@ def run_safr(args):
             "throughput_back_to_back": {
                 "cold_B": {"frames_per_s": args.steps / (total_ms * 1e-3), "us_per_frame": 1e6 * cold_s,
                            "host_submit_us_per_frame": 1e6 * cold_host_s / args.steps,
+                           "all_queued_before_gpu_start": cold_host_s < cold_sleep_s,
                            "how": f"{args.steps} frames back to back over {args.pool} plans of the workload "
                                   f"({args.pool} x 21 MB of B: every frame's B comes from HBM)"},
                 "warm_L2": {"frames_per_s": args.steps / (warm_ms * 1e-3), "us_per_frame": 1e6 * warm_s,
                             "host_submit_us_per_frame": 1e6 * warm_host_s / args.steps,
+                            "all_queued_before_gpu_start": warm_host_s < warm_sleep_s,
                             "how": f"{args.steps} frames back to back on one plan (B stays in the L2)"}},
             "kernels_ms": dict(zip(phase_names, ph_mean)), "path": "fused" if launches == 1 else "passes",
             "fused_phases_us": ({k: float(np.median([st[k] for st in stamps])) for k in stamps[0]}
@@ -854,8 +871,9 @@ def run_safr(args):
                          "algorithmic_bytes": k_bytes,
                          "duration": "mean launch time of the back-to-back frames over the plan pool"},
             "roofline_l2": {"bound": "l2+hbm", "bw_l2_gbs": bw_l2, "bw_hbm_gbs": hbm,
-                            "bw_l2_how": "plain device copy (torch copy_) with source and destination resident "
-                                         "in the L2, read + write bytes / CUDA-event time; best of "
+                            "bw_l2_how": "plain device copy (torch copy_, 40 copies in one CUDA graph) with source "
+                                         "and destination resident in the L2, read + write bytes / CUDA-event "
+                                         "time; best of "
                                          + ", ".join(f"{r['mb_each']} MB ({r['gbs']:.0f} GB/s)" for r in l2_rows),
                             "t_roof_us": 1e6 * t_roof_l2, "achieved_us": 1e6 * warm_s,
                             "frac": t_roof_l2 / warm_s,

@@ -78,9 +78,14 @@ enum { SAFR_NATIVE = 0, SAFR_METRIC = 1 };                     /* output grid   
 
 /* Kernel schedules of safr_reconstruct (safr_set_path). */
 enum {
-    SAFR_PATH_AUTO = 0,  /* the persistent kernel when the plan fits it, else the three passes */
-    SAFR_PATH_FUSED = 1, /* one persistent cooperative kernel with two grid barriers          */
-    SAFR_PATH_PASSES = 2 /* three kernels chained by programmatic dependent launch           */
+    SAFR_PATH_AUTO = 0,    /* the one-cluster kernel on small plans (grids up to 64 whose last two
+                              phases take one round of transforms per CTA), else the persistent
+                              kernel when it fits, else the three passes                        */
+    SAFR_PATH_FUSED = 1,   /* one persistent cooperative kernel with two grid barriers          */
+    SAFR_PATH_PASSES = 2,  /* three kernels chained by programmatic dependent launch           */
+    SAFR_PATH_CLUSTER = 3  /* grids up to 64: one thread-block cluster of up to 16 CTAs holds the
+                              whole frame in shared memory; the CTAs exchange the row and column
+                              spectra through distributed shared memory and two cluster barriers */
 };
 
 /* Warning bits of safr_plan_info.warnings. */
@@ -123,7 +128,7 @@ typedef struct {
     size_t out_bytes;       /* bytes of one frame of layers                       */
     int warnings;           /* SAFR_WARN_* bits                                   */
     int precomputed;        /* 1 after safr_precompute                            */
-    int path;               /* schedule safr_reconstruct uses: SAFR_PATH_FUSED or SAFR_PATH_PASSES */
+    int path;               /* schedule safr_reconstruct uses: SAFR_PATH_CLUSTER, _FUSED or _PASSES */
     int tile_rows;          /* output rows per phase-3 item of the persistent kernel */
     int autotuned;          /* 1 after safr_autotune                              */
 } safr_plan_info;
@@ -228,13 +233,23 @@ safr_status safr_trace_read(safr_plan_t plan, float *ms, int n, int *n_out);
  *   10 phase 2: B block landed        22 phase 3 done
  *   11 phase 2: first apply done
  * (marks 2-4, 8-13 and 17-21 are taken on the CTA's first batch, column or
- * item).  Writes up to `n` values; *n_out = 23.  SAFR_ERR_INVALID_ARG if
- * there is no traced persistent-kernel frame.
+ * item).  For a SAFR_PATH_CLUSTER frame the marks are:
+ *    0 start                          7 phase 2: first column done
+ *    1 prologue issued                8 phase 2 done
+ *    2 phase 1: frame data in         9 cluster barrier 2 passed
+ *    3 phase 1 done                  10 phase 3: first round transformed
+ *    4 cluster barrier 1 passed      11 phase 3 done
+ *    5 phase 2: star transforms done 12 last cluster barrier passed
+ *    6 phase 2: B landed             13 bulk copies issued (thread 0)
+ *                                    15 phase 3: first round stored
+ * and marks 14, 16-22 are 0.  Writes up to `n` values; *n_out = 23.
+ * SAFR_ERR_INVALID_ARG if there is no traced persistent-kernel or one-cluster
+ * frame.
  */
 safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out);
 
 /*
- * The raw timestamps of the last traced persistent-kernel frame: us[b * 23 + i]
+ * The raw timestamps of the last traced persistent-kernel or one-cluster frame: us[b * 23 + i]
  * = mark i of CTA b in microseconds from the earliest CTA start (0 where the
  * CTA never reached the mark), for the n_cta CTAs of the launch; writes at
  * most n values, *n_cta = the grid size.  Errors as safr_trace_phases.
@@ -245,11 +260,13 @@ safr_status safr_trace_stamps(safr_plan_t plan, double *us, int n, int *n_cta);
 int safr_launches_per_frame(safr_plan_t plan);
 
 /*
- * Choose the kernel schedule of the next calls (SAFR_PATH_*).  Both schedules
- * compute the same layers.  SAFR_PATH_FUSED on a plan the persistent kernel
- * cannot hold returns SAFR_ERR_UNSUPPORTED_SIZE and leaves the choice as it
- * was.  safr_get_path returns the schedule that safr_reconstruct will use
- * (SAFR_PATH_FUSED or SAFR_PATH_PASSES), or -1 for a NULL plan.
+ * Choose the kernel schedule of the next calls (SAFR_PATH_*).  Every schedule
+ * computes the same layers.  SAFR_PATH_FUSED on a plan the persistent kernel
+ * cannot hold, or SAFR_PATH_CLUSTER on a plan the one-cluster kernel cannot
+ * hold (grids above 64, or shared memory), returns SAFR_ERR_UNSUPPORTED_SIZE
+ * and leaves the choice as it was.  safr_get_path returns the schedule that
+ * safr_reconstruct will use (SAFR_PATH_CLUSTER, SAFR_PATH_FUSED or
+ * SAFR_PATH_PASSES), or -1 for a NULL plan.
  */
 safr_status safr_set_path(safr_plan_t plan, int path);
 

@@ -419,6 +419,8 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
         return SAFR_ERR_UNSUPPORTED_SIZE;
     p->fused_ok = safr::configure_fused(p) ? 1 : 0;
     cudaGetLastError();
+    p->cl_ok = safr::configure_cluster(p) ? 1 : 0;
+    cudaGetLastError();
 #undef SAFR_TRY
     return SAFR_OK;
 }
@@ -426,6 +428,7 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
 cudaError_t dispatch(safr_plan_s *p, const void *in, const float *in_scales, void *out, float *out_scales,
                      cudaStream_t st)
 {
+    if (safr::use_cluster(p)) return safr::launch_cluster(p, in, in_scales, out, out_scales, st);
     if (safr::use_fused(p)) return safr::launch_fused(p, in, in_scales, out, out_scales, st);
     return safr::launch_frame(p, in, in_scales, out, out_scales, st);
 }
@@ -575,7 +578,7 @@ safr_status safr_get_plan_info(safr_plan_t plan, safr_plan_info *info)
     info->out_bytes = plan->out_bytes;
     info->warnings = plan->warnings;
     info->precomputed = plan->precomputed;
-    info->path = safr::use_fused(plan) ? SAFR_PATH_FUSED : SAFR_PATH_PASSES;
+    info->path = safr::path_in_use(plan);
     info->tile_rows = plan->f2_rt3;
     info->autotuned = plan->autotuned;
     return SAFR_OK;
@@ -658,23 +661,25 @@ safr_status safr_trace_phases(safr_plan_t plan, double *us, int n, int *n_out)
 {
     if (!plan || (!us && n > 0)) return SAFR_ERR_INVALID_ARG;
     if (n_out) *n_out = 0;
-    if (!plan->traced || !safr::use_fused(plan) || !plan->d_stamps) return SAFR_ERR_INVALID_ARG;
+    if (!plan->traced || !(safr::use_fused(plan) || safr::use_cluster(plan)) || !plan->d_stamps)
+        return SAFR_ERR_INVALID_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
     if (cudaEventSynchronize(plan->ev[1]) != cudaSuccess) return SAFR_ERR_CUDA;
     const int K = SAFR_TRACE_MARKS;
-    std::vector<unsigned long long> st((size_t)plan->f2_grid * K);
+    const int grid = safr::use_cluster(plan) ? plan->cl_cs : plan->f2_grid;
+    std::vector<unsigned long long> st((size_t)grid * K);
     if (cudaMemcpy(st.data(), plan->d_stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
         return SAFR_ERR_CUDA;
     // mark i: latest CTA to reach it, in microseconds from the earliest CTA start
     // (marks a CTA never reaches, e.g. a CTA with no phase-2 column, stay 0)
     unsigned long long t0 = ~0ull;
-    for (int b = 0; b < plan->f2_grid; ++b) t0 = std::min(t0, st[(size_t)b * K]);
+    for (int b = 0; b < grid; ++b) t0 = std::min(t0, st[(size_t)b * K]);
     double v[SAFR_TRACE_MARKS];
     for (int i = 0; i < K; ++i) {
         unsigned long long last = 0;
-        for (int b = 0; b < plan->f2_grid; ++b) last = std::max(last, st[(size_t)b * K + i]);
+        for (int b = 0; b < grid; ++b) last = std::max(last, st[(size_t)b * K + i]);
         v[i] = last > t0 ? 1e-3 * (double)(last - t0) : 0.0;
     }
     for (int i = 0; i < K && i < n; ++i) us[i] = v[i];
@@ -686,26 +691,29 @@ safr_status safr_trace_stamps(safr_plan_t plan, double *us, int n, int *n_cta)
 {
     if (!plan || (!us && n > 0)) return SAFR_ERR_INVALID_ARG;
     if (n_cta) *n_cta = 0;
-    if (!plan->traced || !safr::use_fused(plan) || !plan->d_stamps) return SAFR_ERR_INVALID_ARG;
+    if (!plan->traced || !(safr::use_fused(plan) || safr::use_cluster(plan)) || !plan->d_stamps)
+        return SAFR_ERR_INVALID_ARG;
     DeviceGuard guard(plan->device);
     if (!guard.ok) return SAFR_ERR_CUDA;
     if (cudaEventSynchronize(plan->ev[1]) != cudaSuccess) return SAFR_ERR_CUDA;
     const int K = SAFR_TRACE_MARKS;
-    std::vector<unsigned long long> st((size_t)plan->f2_grid * K);
+    const int grid = safr::use_cluster(plan) ? plan->cl_cs : plan->f2_grid;
+    std::vector<unsigned long long> st((size_t)grid * K);
     if (cudaMemcpy(st.data(), plan->d_stamps, st.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
         cudaSuccess)
         return SAFR_ERR_CUDA;
     unsigned long long t0 = ~0ull;
-    for (int b = 0; b < plan->f2_grid; ++b) t0 = std::min(t0, st[(size_t)b * K]);
+    for (int b = 0; b < grid; ++b) t0 = std::min(t0, st[(size_t)b * K]);
     for (size_t i = 0; i < st.size() && (long)i < n; ++i) us[i] = st[i] > t0 ? 1e-3 * (double)(st[i] - t0) : 0.0;
-    if (n_cta) *n_cta = plan->f2_grid;
+    if (n_cta) *n_cta = grid;
     return SAFR_OK;
 }
 
 safr_status safr_set_path(safr_plan_t plan, int path)
 {
-    if (!plan || path < SAFR_PATH_AUTO || path > SAFR_PATH_PASSES) return SAFR_ERR_INVALID_ARG;
+    if (!plan || path < SAFR_PATH_AUTO || path > SAFR_PATH_CLUSTER) return SAFR_ERR_INVALID_ARG;
     if (path == SAFR_PATH_FUSED && !plan->fused_ok) return SAFR_ERR_UNSUPPORTED_SIZE;
+    if (path == SAFR_PATH_CLUSTER && !plan->cl_ok) return SAFR_ERR_UNSUPPORTED_SIZE;
     plan->path = path;
     plan->traced = 0;
     return SAFR_OK;
@@ -750,7 +758,7 @@ safr_status safr_set_tile_rows(safr_plan_t plan, int rows)
 int safr_get_path(safr_plan_t plan)
 {
     if (!plan) return -1;
-    return safr::use_fused(plan) ? SAFR_PATH_FUSED : SAFR_PATH_PASSES;
+    return safr::path_in_use(plan);
 }
 
 safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s)

@@ -98,9 +98,13 @@ safr_status enqueue_frames(safr_batch_s *b, const void *const *in, const float *
 }
 
 // Frames that may run K at a time: persistent-kernel plans of grids up to 256 (latency-bound: on
-// 1/K of the SMs each, K of them finish sooner than one after the other).  Larger frames run alone
-// on the whole GPU.  A plan that appears twice keeps the batch sequential.
-bool concurrent_frame(const safr_plan_s *pl) { return safr::use_fused(pl) && pl->M <= 256; }
+// 1/K of the SMs each, K of them finish sooner than one after the other), and one-cluster plans
+// (a cluster of at most 16 SMs each).  Larger frames run alone on the whole GPU.  A plan that
+// appears twice keeps the batch sequential.
+bool concurrent_frame(const safr_plan_s *pl)
+{
+    return (safr::use_fused(pl) && pl->M <= 256) || safr::use_cluster(pl);
+}
 
 int concurrent_count(const safr_batch_s *b)
 {
@@ -139,7 +143,7 @@ bool capture_k(safr_batch_s *b, int K, const void *const *in, const float *const
     bool conf_ok = true;
     if (K > 1)
         for (safr_plan_s *pl : b->plans)
-            if (concurrent_frame(pl)) {
+            if (concurrent_frame(pl) && safr::use_fused(pl)) {  // a one-cluster frame keeps its cluster
                 saved.push_back({pl, pl->f2_grid_force, pl->f2_rt_force});
                 pl->f2_grid_force = nsm / K;
                 pl->f2_rt_force = pl->f2_rt3;
@@ -314,7 +318,7 @@ safr_status safr_batch_reconstruct(safr_batch_t b, const void *const *d_wavefron
         key.push_back(isc);
         key.push_back(d_layers[i]);
         key.push_back(osc);
-        key.push_back((const void *)(uintptr_t)(safr::use_fused(pl) ? 1 + pl->f2_rt3 : 0));
+        key.push_back((const void *)(uintptr_t)(safr::use_cluster(pl) ? 1 : (safr::use_fused(pl) ? 2 + pl->f2_rt3 : 0)));
         key.push_back((const void *)(uintptr_t)pl->f2_smem);
     }
     BatchDeviceGuard guard(b->device);
@@ -412,8 +416,10 @@ extern "C" safr_status safr_autotune(safr_plan_t pl, cudaStream_t stream)
             return SAFR_OK;
         }
     }
-    // candidates: the persistent kernel with every feasible phase-3 tile height, the three passes
+    // candidates: the one-cluster kernel, the persistent kernel with every feasible phase-3 tile
+    // height, the three passes
     std::vector<std::pair<int, int>> cand;
+    if (pl->cl_ok) cand.emplace_back(SAFR_PATH_CLUSTER, 0);
     if (pl->fused_ok)
         for (int rt = std::min(32, pl->M); rt >= 2; rt -= 2)
             if (apply_schedule(pl, SAFR_PATH_FUSED, rt) && pl->f2_rt3 == rt) cand.emplace_back(SAFR_PATH_FUSED, rt);
@@ -430,7 +436,7 @@ extern "C" safr_status safr_autotune(safr_plan_t pl, cudaStream_t stream)
     if (st == SAFR_OK && (cudaMemsetAsync(d_in, 0, pl->in_bytes, stream) != cudaSuccess ||
                           cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = SAFR_ERR_CUDA;
-    std::pair<int, int> best(pl->fused_ok ? SAFR_PATH_FUSED : SAFR_PATH_PASSES, 0);
+    std::pair<int, int> best(pl->cl_ok ? SAFR_PATH_CLUSTER : (pl->fused_ok ? SAFR_PATH_FUSED : SAFR_PATH_PASSES), 0);
     float best_ms = 1e30f;
     const int trace = pl->trace;
     pl->trace = 0;

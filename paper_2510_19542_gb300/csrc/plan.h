@@ -109,6 +109,12 @@ struct safr_plan_s {
     int f2_ck = 1;              // phase-2 columns per pass
     int f2_ck_allow = 1;        // 0: one column per pass (schedule choice)
     int autotuned = 0;          // 1 after safr_autotune
+    // one-cluster kernel for grids up to 64 (cluster_impl.cuh)
+    int cl_ok = 0;              // the one-cluster kernel fits this plan
+    int cl_auto = 0;            // ... and SAFR_PATH_AUTO prefers it
+    int cl_cs = 0, cl_ncol = 0, cl_slots1 = 0, cl_stage_b = 0;
+    unsigned cl_off[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    size_t cl_smem = 0;
     int debug_skip_cta = -1;
     unsigned long long barrier_timeout_ns = 1000000000ull;  // 1 s
     int gmax = 16; // compile-time bound on stars per group of the column pass
@@ -170,8 +176,22 @@ void filter_invalidate(safr_plan_s *plan);  // the SVD basis is stale (the geome
 void polc_table(const safr_plan_s *plan, std::vector<unsigned char> &bytes);
 std::vector<double> pre_inputs(const safr_plan_s *plan);    // refresh.cpp
 int containment_warnings(const safr_plan_s *plan);          // refresh.cpp
+bool configure_cluster(safr_plan_s *plan);
+cudaError_t launch_cluster(safr_plan_s *plan, const void *in, const float *in_scales, void *out, float *out_scales,
+                           cudaStream_t stream);
+// the schedule safr_reconstruct runs: the one-cluster kernel when the plan fits it and the path is
+// SAFR_PATH_CLUSTER, or SAFR_PATH_AUTO on a plan small enough for it; else the persistent kernel
+// when it fits and the path is not SAFR_PATH_PASSES; else the three passes
+inline bool use_cluster(const safr_plan_s *plan)
+{
+    return plan->cl_ok && (plan->path == SAFR_PATH_CLUSTER || (plan->path == SAFR_PATH_AUTO && plan->cl_auto));
+}
 inline bool use_fused(const safr_plan_s *plan)
 {
-    return plan->fused_ok && plan->path != SAFR_PATH_PASSES;
+    return plan->fused_ok && !use_cluster(plan) && plan->path != SAFR_PATH_PASSES;
+}
+inline int path_in_use(const safr_plan_s *plan)
+{
+    return use_cluster(plan) ? SAFR_PATH_CLUSTER : (use_fused(plan) ? SAFR_PATH_FUSED : SAFR_PATH_PASSES);
 }
 }  // namespace safr

@@ -387,7 +387,7 @@ static FrameParams<R> make_params(safr_plan_s *pl, const void *in, const float *
     return fp;
 }
 
-int launches_per_frame(const safr_plan_s *pl) { return use_fused(pl) ? 1 : 3; }
+int launches_per_frame(const safr_plan_s *pl) { return use_fused(pl) || use_cluster(pl) ? 1 : 3; }
 
 // column-pass instance for the largest star group of the plan
 template <typename R>

@@ -30,7 +30,7 @@ SAFR_NGS, SAFR_LGS = 0, 1
 SAFR_FP32, SAFR_FP16_STORAGE, SAFR_FP64 = 0, 1, 2
 SAFR_NATIVE, SAFR_METRIC = 0, 1
 SAFR_WARN_CONTAINMENT = 1
-SAFR_PATH_AUTO, SAFR_PATH_FUSED, SAFR_PATH_PASSES = 0, 1, 2
+SAFR_PATH_AUTO, SAFR_PATH_FUSED, SAFR_PATH_PASSES, SAFR_PATH_CLUSTER = 0, 1, 2, 3
 
 _PRECISION = {"fp32": SAFR_FP32, "fp16": SAFR_FP16_STORAGE, "fp64": SAFR_FP64}
 _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_reconstruct_host",
@@ -266,14 +266,20 @@ def safr_trace_read(plan: int):
 
 
 def safr_trace_phases(plan: int):
-    """Phase completion times (us) of the last traced persistent-kernel frame."""
+    """Phase completion times (us) of the last traced persistent-kernel or one-cluster frame."""
     us = (C.c_double * 32)()
     n = C.c_int(0)
     _check(load().safr_trace_phases(plan, us, 32, C.byref(n)), "safr_trace_phases")
-    keys = ["start", "prologue", "p1_data_in", "p1_B_issued", "p1_fft", "p1_done", "bar1_arrive", "bar1_out",
-            "p2_star_fft", "p2_synced", "p2_B_landed", "p2_apply", "p2_inv_fft", "p2_stored", "p2_done",
-            "bar2_arrive", "bar2_out", "p3_tables", "p3_staged", "p3_fft", "p3_synced", "p3_first_stored", "p3_done"]
-    return dict(zip(keys, [us[i] for i in range(n.value)]))
+    if safr_get_path(plan) == SAFR_PATH_CLUSTER:
+        keys = ["start", "prologue", "p1_data_in", "p1_done", "bar1_out", "p2_star_fft", "p2_B_landed",
+                "p2_first_column", "p2_done", "bar2_out", "p3_first_round", "p3_done", "end", "copies_issued",
+                "unused", "p3_first_stored"]
+    else:
+        keys = ["start", "prologue", "p1_data_in", "p1_B_issued", "p1_fft", "p1_done", "bar1_arrive", "bar1_out",
+                "p2_star_fft", "p2_synced", "p2_B_landed", "p2_apply", "p2_inv_fft", "p2_stored", "p2_done",
+                "bar2_arrive", "bar2_out", "p3_tables", "p3_staged", "p3_fft", "p3_synced", "p3_first_stored",
+                "p3_done"]
+    return dict(zip(keys, [us[i] for i in range(min(n.value, len(keys)))]))
 
 
 def safr_set_grid(plan: int, ctas: int):

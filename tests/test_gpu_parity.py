@@ -36,16 +36,23 @@ DT = {"fp32": np.float32, "fp16": np.float16, "fp64": np.float64}
 from layer_errors import assert_layers, rel_errors  # noqa: E402,F401
 
 
-PATHS = {"fused": 1, "passes": 2}
+PATHS = {"fused": 1, "passes": 2, "cluster": 3}
 
 
-@pytest.fixture(params=["fused", "passes"])
+@pytest.fixture(params=["fused", "passes", "cluster"])
 def path(request):
     return PATHS[request.param]
 
 
+def skip_unless_path_holds(geom, path):
+    """The one-cluster schedule holds grids up to 64 only."""
+    if path == PATHS["cluster"] and geom["M"] > 64:
+        pytest.skip("the one-cluster kernel holds grids up to 64")
+
+
 def run_gpu(safr, geom, x, in_scales=None, path=None):
     prec = geom.get("precision", "fp32")
+    skip_unless_path_holds(geom, path)
     plan = safr.Plan(geom, device=0, path=path)
     if path is not None:
         assert safr.safr_get_path(plan.handle) == path
@@ -115,11 +122,12 @@ def test_tiny_ngs_fp32(safr, synth, oracle_mod, path):
 
 
 @pytest.mark.parametrize("M,P,L", [(64, 20, None), (128, 40, None), (64, 37, 5), (32, 9, 3), (8, 8, 2),
-                                   (16, 5, 9), (256, 80, 12), (512, 160, 6)])
+                                   (16, 5, 9), (256, 80, 12), (512, 160, 6), (64, 20, 35)])
 def test_mixed_lgs_ngs_fp32(safr, synth, oracle_mod, M, P, L, path):
     """Split tomography with removeTT and the metric resample; odd P gives a
     ragged last row pair and an odd pad offset.  The 512 grid runs the
-    transforms with 16 values per lane (loaded 8 at a time) and B unstaged."""
+    transforms with 16 values per lane (loaded 8 at a time) and B unstaged;
+    the 64 grid with 35 layers has B unstaged in the one-cluster kernel."""
     g = synth.scaled(synth.config(2), M=M, P=P, L=L)
     check(safr, oracle_mod, g, synth.frame(g), path=path)
 
@@ -210,6 +218,7 @@ def test_full_size_fp16_512(safr, synth, oracle_mod, path):
 def test_deterministic_and_host_entry(safr, synth, path):
     g = synth.scaled(synth.config(2), M=64, P=20)
     x = synth.frame(g).astype(np.float32)
+    skip_unless_path_holds(g, path)
     plan = safr.Plan(g, device=0, path=path)
     xin = torch.from_numpy(x).cuda()
     a = plan.reconstruct(xin).cpu().numpy()
@@ -246,7 +255,7 @@ def test_runtime_argument_errors(safr, synth):
 
 
 def test_trace_phases(safr, synth, path):
-    g = synth.config(2)
+    g = synth.config(2) if path != PATHS["cluster"] else synth.scaled(synth.config(2), M=64, P=20)
     plan = safr.Plan(g, device=0, path=path)
     x = torch.from_numpy(synth.random_frame(g, 1).astype(np.float32)).cuda()
     safr.safr_trace(plan.handle, True)
@@ -254,6 +263,32 @@ def test_trace_phases(safr, synth, path):
     ms = safr.safr_trace_read(plan.handle)
     assert len(ms) == safr.safr_launches_per_frame(plan.handle) and all(m > 0 for m in ms)
     plan.close()
+
+
+def test_cluster_kernel_path_selection(safr, synth):
+    """SAFR_PATH_CLUSTER is accepted on grids up to 64 and refused above (choice
+    unchanged); SAFR_PATH_AUTO runs the one-cluster kernel on the small 32-grid
+    frame and the persistent kernel on grids above 64."""
+    g = synth.config(1)
+    plan = safr.Plan(g, device=0)
+    assert safr.safr_get_path(plan.handle) == PATHS["cluster"]
+    assert safr.safr_launches_per_frame(plan.handle) == 1
+    plan.close()
+    for M in (8, 16, 32, 64, 128):
+        g = synth.scaled(synth.config(2), M=M, P=max(4, M // 3))
+        plan = safr.Plan(g, device=0)
+        auto = safr.safr_get_path(plan.handle)
+        if M > 64:
+            assert auto == PATHS["fused"]
+            with pytest.raises(safr.SafrError) as ei:
+                safr.safr_set_path(plan.handle, PATHS["cluster"])
+            assert ei.value.status == safr.SAFR_ERR_UNSUPPORTED_SIZE
+            assert safr.safr_get_path(plan.handle) == auto
+        else:
+            assert auto in (PATHS["cluster"], PATHS["fused"])
+            safr.safr_set_path(plan.handle, PATHS["cluster"])
+            assert safr.safr_get_path(plan.handle) == PATHS["cluster"]
+        plan.close()
 
 
 def test_paths_agree(safr, synth):
