@@ -340,7 +340,12 @@ safr_status safr_debug_skip_barrier(safr_plan_t plan, int cta, double timeout_s)
  *
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  Every call on a device shares the one array,
+ * before any stream capture.  The first call with a given (device, M, P, L,
+ * G) also sizes the kernel's launch (kernel attributes and occupancy
+ * queries); later calls with that shape reuse it from a fixed table of 32
+ * shapes and make no query.  Launch failures are returned as SAFR_ERR_CUDA
+ * from the launch calls' own status; an error the caller had pending is
+ * neither read nor cleared.  Every call on a device shares the one array,
  * and each call re-initialises the parts that must start from zero.  Calls
  * that overlap on the GPU (other streams, or other threads) race on it and
  * give wrong layers.  Asynchronous on `stream`; argument errors are returned
@@ -398,12 +403,18 @@ safr_status safr_batch_get_status(safr_batch_t batch);
 int safr_batch_launches(safr_batch_t batch);
 int safr_batch_graph(safr_batch_t batch);
 /* Concurrent chains of the batch's graph: frames of grids up to 256 on the
- * persistent kernel may run K at a time, each on 1/K of the SMs, with the
- * larger frames first on the whole GPU.  K in {1, 2, 4, 8} is chosen at the
+ * persistent kernel may run K at a time, each on 1/K of the SMs (one-cluster
+ * frames keep their cluster), with the larger frames first on the whole GPU.  K in {1, 2, 4, 8} is chosen at the
  * first capture by timing each graph (that call replays the batch a few times
  * on its own stream and synchronises); the layers do not depend on K.
  * Returns 0 before the first call. */
 int safr_batch_chains(safr_batch_t batch);
+/* Force the chain count K of the next captures (1, 2, 4 or 8), or 0 to choose
+ * it again by timing at the next capture; the next call captures the graph
+ * again.  A batch with fewer than two concurrent frames (or a plan that appears
+ * twice) keeps one chain whatever is asked.  SAFR_ERR_INVALID_ARG for other
+ * values or a NULL batch. */
+safr_status safr_batch_set_chains(safr_batch_t batch, int chains);
 safr_status safr_batch_destroy(safr_batch_t batch);
 
 /*

@@ -360,6 +360,14 @@ int safr_batch_graph(safr_batch_t b) { return b && b->exec ? 1 : 0; }
 
 int safr_batch_chains(safr_batch_t b) { return b ? b->chains : 0; }
 
+safr_status safr_batch_set_chains(safr_batch_t b, int chains)
+{
+    if (!b || !(chains == 0 || chains == 1 || chains == 2 || chains == 4 || chains == 8)) return SAFR_ERR_INVALID_ARG;
+    b->chains = chains;
+    b->key.clear();  // the next call captures the graph again
+    return SAFR_OK;
+}
+
 safr_status safr_batch_destroy(safr_batch_t b)
 {
     if (!b) return SAFR_ERR_INVALID_ARG;

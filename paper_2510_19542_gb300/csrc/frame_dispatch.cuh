@@ -28,8 +28,21 @@ struct Frame2Inst {
     {
         Frame2Params<R> fp = Frame2Host<M, R>::params(pl, in, isc, out, osc);
         void *args[] = {&fp};
-        return cudaLaunchCooperativeKernel(kernel_ck(pl->f2_ck), dim3(pl->f2_grid), dim3(frame2_threads(M)), args,
-                                           pl->f2_smem, st);
+        // one CTA per SM at most (configure), so every CTA of the grid is resident once the SMs are
+        // free; launched as an ordinary kernel with programmatic stream serialization so that a frame
+        // right after another one overlaps its launch and prologue with that frame's end (a
+        // cooperative launch does not overlap)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(pl->f2_grid);
+        cfg.blockDim = dim3(frame2_threads(M));
+        cfg.dynamicSmemBytes = pl->f2_smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelExC(&cfg, kernel_ck(pl->f2_ck), args);
     }
 };
 

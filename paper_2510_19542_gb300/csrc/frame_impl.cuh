@@ -1,8 +1,12 @@
 // Algorithm 1 as ONE persistent cooperative kernel per frame, for a grid
 // size M fixed at compile time (instantiated per precision in frame_*.cu).
 //
-// All CTAs are co-resident (cooperative launch, one per SM, 512 threads) and
-// run three phases separated by two grid-wide barriers.  Every transform is a
+// All CTAs are co-resident (one per SM, 512 threads: the grid is at most the
+// SM count and the kernel's shared memory allows one CTA per SM) and run three
+// phases separated by two grid-wide barriers.  The kernel is launched with
+// programmatic stream serialization: a frame launched right after another
+// one takes the SMs as that frame's CTAs leave, runs its prologue (tables, B
+// copy), and waits (griddepcontrol.wait) before it reads its inputs.  Every transform is a
 // warp-level FFT (warpfft.cuh): one group of min(M, 32) lanes per transform,
 // all data in registers, lanes exchanged by shuffles.
 //
@@ -283,13 +287,23 @@ __device__ __noinline__ void polc_phase(const Frame2Params<R> &fp, int G, int L,
     }
 }
 
+// Reads, at the start of a launch (thread 0), the arrival count the counter held when the previous
+// launch on it ended.  That launch wrote it; stream order makes the write visible, so a plain load
+// does (an acquire load would stall thread 0 until it lands).  After its last grid barrier, CTA 0
+// stores the count plus this launch's arrivals (barriers x its own grid): every CTA has read the old
+// value by then, and the next launch may use another grid size.
+__device__ __forceinline__ unsigned long long bar_count_read(const unsigned long long *bar)
+{
+    return threadIdx.x == 0 ? __ldcg(bar + 1) : 0ull;
+}
 // One frame of Algorithm 1 on the whole grid (all CTAs call it together).
-//   bar_base   arrivals counted on fp.bar before this frame (thread 0)
+//   bar_base   set to the arrivals counted on fp.bar before this frame (thread 0), read once the
+//              kernels before this one in the stream have finished
 //   bph, tph   parities of the B and table mbarriers for this frame's first waits
 //   first      the first frame of the launch: initialises the mbarriers
 // Returns false if a bounded wait gave up (status recorded); the caller then stops.
 template <int M, typename R, typename TIN, typename TOUT, int CKT>
-__device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned long long bar_base, unsigned &bph,
+__device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned long long &bar_base, unsigned &bph,
                                            unsigned tph, bool first_frame)
 {
     using C = typename Frame2Params<R>::C;
@@ -412,6 +426,12 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 prefetch_l2(base + off, min(4096u, colB_bytes - off));
         }
     }
+    // Everything above reads only the plan's own tables and B, which no frame writes.  A frame
+    // launched right after another one starts while that one finishes (programmatic dependent
+    // launch); its inputs, the workspaces and the barrier counter are touched only after the
+    // kernels before it in the stream have finished and their writes are visible.
+    pdl_wait();
+    bar_base = bar_count_read(fp.bar);
     __syncthreads();  // the parameter copies
     SAFR_MARK(1, true);
 
@@ -1004,15 +1024,6 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     return true;
 }
 
-// Reads, at the start of a launch (thread 0), the arrival count the counter held when the previous
-// launch on it ended.  That launch wrote it; stream order makes the write visible, so a plain load
-// does (an acquire load would stall thread 0 until it lands).  After its last grid barrier, CTA 0
-// stores the count plus this launch's arrivals (barriers x its own grid): every CTA has read the old
-// value by then, and the next launch may use another grid size.
-__device__ __forceinline__ unsigned long long bar_count_read(const unsigned long long *bar)
-{
-    return threadIdx.x == 0 ? __ldcg(bar + 1) : 0ull;
-}
 __device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsigned long long base,
                                                   unsigned long long arrivals)
 {
@@ -1020,11 +1031,14 @@ __device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsig
         asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(bar + 1), "l"(base + arrivals) : "memory");
 }
 
-// One frame per launch; CK phase-2 columns per pass.
+// One frame per launch; CK phase-2 columns per pass.  The launch of the next kernel in the stream
+// may begin at once (its CTAs take the SMs this frame's CTAs leave, and it waits for this frame to
+// finish before it touches its data).
 template <int M, typename R, typename TIN, typename TOUT, int CK = 1>
 __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R> fp)
 {
-    const unsigned long long base = bar_count_read(fp.bar);
+    pdl_trigger();
+    unsigned long long base = 0;
     unsigned bph = 0;
     if (frame_body<M, R, TIN, TOUT, CK>(fp, base, bph, 0u, true))
         bar_count_advance(fp.bar, base, 2ull * gridDim.x);

@@ -40,6 +40,19 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void *g_scratch_dev[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
 
+// Launch shapes configured by earlier calls, per (device, M, P, L, G): a later call with the same
+// shape makes no configuration queries (kernel attributes, occupancy).  Fixed size, no heap use;
+// when it is full, the oldest entry is replaced.
+struct ShapeEntry {
+    int dev = -1, M = 0, P = 0, L = 0, G = 0;
+    int grid = 0, stage_b = 0, rt3 = 0, cap3 = 0, tiles3 = 0, n3 = 0, st3[2] = {0, 0}, nsrc3[2] = {0, 0};
+    unsigned off_rs = 0, off_tw = 0, off_b = 0, off_d = 0, off_xy = 0, off_s3 = 0;
+    size_t smem = 0;
+};
+constexpr int kShapes = 32;
+ShapeEntry g_shapes[kShapes];
+int g_shapes_next = 0;
+
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Warp-FFT twiddles from FP64 sincospi: W_M^(t k) at [k * LW + t] for k < M / LW,
@@ -119,33 +132,68 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
         scratch = (unsigned char *)g_scratch_dev[cuda_device];
     }
 
-    // launch shape of the persistent kernel for one star group (plan on the stack: no heap use)
-    int nsm = 0, coop = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, cuda_device) != cudaSuccess || !coop) {
-        cudaGetLastError();
-        return SAFR_ERR_CUDA;
-    }
-    safr_plan_s pl;
-    pl.device = cuda_device;
-    pl.M = M;
-    pl.P = P;
-    pl.L = L;
-    pl.G = G;
-    pl.Mh = Mh;
-    pl.o = (M - P) / 2;
-    pl.precision = SAFR_FP32;
-    pl.ngroups = 1;
-    pl.grp[0].G = G;
-    pl.grp[0].b_row0 = 0;
-    pl.grp[0].resample = false;
-    pl.sumLG = L * G;
-    if (!safr::frame2_configure_f32(&pl, nsm)) {
-        cudaGetLastError();
-        return SAFR_ERR_UNSUPPORTED_SIZE;
-    }
+    // launch shape of the persistent kernel for one star group: from the cache, else configured on a
+    // plan on the stack (no heap use) and cached
     void *kernel = safr::frame2_kernel_f32(M);
     if (!kernel) return SAFR_ERR_UNSUPPORTED_SIZE;
+    ShapeEntry sh;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        for (const ShapeEntry &e : g_shapes)
+            if (e.dev == cuda_device && e.M == M && e.P == P && e.L == L && e.G == G) {
+                sh = e;
+                cached = true;
+                break;
+            }
+    }
+    if (!cached) {
+        int nsm = 0, coop = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, cuda_device) != cudaSuccess ||
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, cuda_device) != cudaSuccess || !coop)
+            return SAFR_ERR_CUDA;
+        safr_plan_s pl;
+        pl.device = cuda_device;
+        pl.M = M;
+        pl.P = P;
+        pl.L = L;
+        pl.G = G;
+        pl.Mh = Mh;
+        pl.o = (M - P) / 2;
+        pl.precision = SAFR_FP32;
+        pl.ngroups = 1;
+        pl.grp[0].G = G;
+        pl.grp[0].b_row0 = 0;
+        pl.grp[0].resample = false;
+        pl.sumLG = L * G;
+        pl.f2_ck_allow = 0;  // the one-column kernel instance is the one launched below
+        if (!safr::frame2_configure_f32(&pl, nsm)) return SAFR_ERR_UNSUPPORTED_SIZE;
+        sh.dev = cuda_device;
+        sh.M = M;
+        sh.P = P;
+        sh.L = L;
+        sh.G = G;
+        sh.grid = pl.f2_grid;
+        sh.stage_b = pl.f2_stage_b;
+        sh.rt3 = pl.f2_rt3;
+        sh.cap3 = pl.f2_cap3;
+        sh.tiles3 = pl.f2_tiles3;
+        sh.n3 = pl.f2_n3;
+        for (int gi = 0; gi < 2; ++gi) {
+            sh.st3[gi] = pl.f2_st3[gi];
+            sh.nsrc3[gi] = pl.f2_nsrc3[gi];
+        }
+        sh.off_rs = pl.f2_off_rs;
+        sh.off_tw = pl.f2_off_tw;
+        sh.off_b = pl.f2_off_b;
+        sh.off_d = pl.f2_off_d;
+        sh.off_xy = pl.f2_off_xy;
+        sh.off_s3 = pl.f2_off_s3;
+        sh.smem = pl.f2_smem;
+        std::lock_guard<std::mutex> lock(g_setup_mutex);
+        g_shapes[g_shapes_next] = sh;
+        g_shapes_next = (g_shapes_next + 1) % kShapes;
+    }
 
     using C = float2;
     safr::Frame2Params<float> fp;
@@ -153,32 +201,32 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
     fp.P = P;
     fp.L = L;
     fp.G = G;
-    fp.o = pl.o;
+    fp.o = (M - P) / 2;
     fp.ngroups = 1;
     fp.sumLG = L * G;
     fp.npr = (P + 1) / 2;
     fp.n1 = G * fp.npr;
     fp.ntask2 = L;
-    fp.rt3 = pl.f2_rt3;
-    fp.cap3 = pl.f2_cap3;
-    fp.tiles3 = pl.f2_tiles3;
-    fp.n3 = pl.f2_n3;
+    fp.rt3 = sh.rt3;
+    fp.cap3 = sh.cap3;
+    fp.tiles3 = sh.tiles3;
+    fp.n3 = sh.n3;
     for (int gi = 0; gi < 2; ++gi) {
-        fp.st3[gi] = pl.f2_st3[gi];
-        fp.nsrc3[gi] = pl.f2_nsrc3[gi];
+        fp.st3[gi] = sh.st3[gi];
+        fp.nsrc3[gi] = sh.nsrc3[gi];
     }
     fp.any_tt = 0;
     fp.any_resample = 0;
-    fp.stage_b = pl.f2_stage_b;
+    fp.stage_b = sh.stage_b;
     fp.skip_cta = -1;
     fp.timeout_ns = 1000000000ull;
     fp.inv_M2 = (float)(1.0 / ((double)M * M));
-    fp.off_rs = pl.f2_off_rs;
-    fp.off_tw = pl.f2_off_tw;
-    fp.off_b = pl.f2_off_b;
-    fp.off_d = pl.f2_off_d;
-    fp.off_xy = pl.f2_off_xy;
-    fp.off_s3 = pl.f2_off_s3;
+    fp.off_rs = sh.off_rs;
+    fp.off_tw = sh.off_tw;
+    fp.off_b = sh.off_b;
+    fp.off_d = sh.off_d;
+    fp.off_xy = sh.off_xy;
+    fp.off_s3 = sh.off_s3;
     fp.in = d_wavefronts;
     fp.out = d_layers;
     fp.B = (const C *)d_B;
@@ -192,14 +240,17 @@ extern "C" safr_status safr_reconstruct_noalloc(int cuda_device, int M, int P, i
     fp.grp[0].resample = 0;
     for (int g = 0; g < G; ++g) fp.grp[0].star[g] = g;
 
-    k_noalloc_prepare<<<(M + LW + 255) / 256, 256, 0, stream>>>((float2 *)(scratch + off_twq), M, LW,
-                                                                  (unsigned long long *)scratch);
-    if (cudaGetLastError() != cudaSuccess) return SAFR_ERR_CUDA;
-    void *args[] = {&fp};
-    if (cudaLaunchCooperativeKernel(kernel, dim3(pl.f2_grid), dim3(safr::frame2_threads(M)), args, pl.f2_smem,
-                                    stream) != cudaSuccess) {
-        cudaGetLastError();
+    // the launches report their own errors (the caller's pending error state is left alone)
+    float2 *twq = (float2 *)(scratch + off_twq);
+    unsigned long long *bar = (unsigned long long *)scratch;
+    int m_arg = M, lw_arg = LW;
+    void *pargs[] = {&twq, &m_arg, &lw_arg, &bar};
+    if (cudaLaunchKernel((const void *)k_noalloc_prepare, dim3((M + LW + 255) / 256), dim3(256), pargs, 0, stream) !=
+        cudaSuccess)
         return SAFR_ERR_CUDA;
-    }
+    void *args[] = {&fp};
+    if (cudaLaunchCooperativeKernel(kernel, dim3(sh.grid), dim3(safr::frame2_threads(M)), args, sh.smem, stream) !=
+        cudaSuccess)
+        return SAFR_ERR_CUDA;
     return SAFR_OK;
 }

@@ -41,7 +41,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
             "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
             "safr_plan_save", "safr_plan_load", "safr_trace_stamps", "safr_set_grid", "safr_get_grid",
-            "safr_batch_chains", "safr_set_tile_rows"]
+            "safr_batch_chains", "safr_set_tile_rows", "safr_batch_set_chains"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -131,6 +131,7 @@ def load(build_if_missing: bool = True):
     lib.safr_batch_launches.argtypes = [vp]
     lib.safr_batch_graph.argtypes = [vp]
     lib.safr_batch_chains.argtypes = [vp]
+    lib.safr_batch_set_chains.argtypes = [vp, C.c_int]
     lib.safr_batch_destroy.argtypes = [vp]
     lib.safr_filter_train.argtypes = [vp, C.POINTER(safr_filter_config), C.POINTER(C.c_float),
                                       C.POINTER(safr_filter_result), vp]
@@ -439,6 +440,11 @@ def safr_batch_launches(batch: int) -> int:
 
 def safr_batch_graph(batch: int) -> int:
     return load().safr_batch_graph(batch)
+
+
+def safr_batch_set_chains(batch: int, chains: int):
+    """Force the batch graph's chain count (1, 2, 4, 8), or 0 to time it again."""
+    _check(load().safr_batch_set_chains(batch, int(chains)), "safr_batch_set_chains")
 
 
 def safr_batch_destroy(batch: int):

@@ -84,6 +84,38 @@ def test_batch_equals_frame_by_frame():
 
 
 @pytest.mark.gpu
+def test_every_chain_count_equals_frame_by_frame():
+    """The batch graph with its chain count forced to K = 1, 2, 4, 8 (frames of grids up to 256 on
+    1/K of the SMs each, one-cluster frames on their own cluster) gives every frame's layers bit
+    for bit as frame-by-frame safr_reconstruct."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2510_19542_gb300 import safr, synth
+    dev = torch.device("cuda:0")
+    geoms = [g for _, g in _geometries(synth) if g.get("precision", "fp32") == "fp32"]
+    geoms += [synth.scaled(synth.config(2), M=128, P=40, L=4), synth.scaled(synth.config(2), M=256, P=80, L=3)]
+    plans = [safr.Plan(g, device=0) for g in geoms]
+    xs = [torch.from_numpy(synth.random_frame(g, 300 + i).astype(np.float32)).to(dev) for i, g in enumerate(geoms)]
+    refs = [p.reconstruct(x).clone() for p, x in zip(plans, xs)]
+    batch = safr.safr_batch_create([p.handle for p in plans])
+    for K in (1, 2, 4, 8):
+        safr.safr_batch_set_chains(batch, K)
+        outs = [p.empty_layers().fill_(float("nan")) for p in plans]
+        safr.safr_batch_reconstruct(batch, xs, outs)
+        torch.cuda.synchronize(dev)
+        assert safr.safr_batch_chains(batch) == K
+        assert safr.safr_batch_graph(batch) == 1
+        for i, (o, r) in enumerate(zip(outs, refs)):
+            assert torch.equal(o, r), (K, geoms[i]["name"])
+    with pytest.raises(safr.SafrError):
+        safr.safr_batch_set_chains(batch, 3)
+    assert safr.safr_batch_get_status(batch) == 0
+    safr.safr_batch_destroy(batch)
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.gpu
 def test_batch_frame_against_oracle(oracle_mod):
     """One batched frame of the seeded uneven-geometry workload (scaled down) against the FP64 oracle."""
     if not torch.cuda.is_available():

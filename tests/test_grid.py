@@ -34,7 +34,7 @@ def test_layers_do_not_depend_on_the_grid(oracle_mod):
         xin = torch.from_numpy(x).to("cuda:0", dt)
         first = None
         # launches on one plan alternate grid sizes: each launch's grid barrier counts its own CTAs
-        for ctas in (0, nsm // 2, nsm // 4, 7, nsm // 2, 0):
+        for ctas in (0, nsm // 2, nsm // 4, nsm // 8, 7, nsm // 2, 0):
             safr.safr_set_grid(p.handle, ctas)
             assert safr.safr_get_grid(p.handle) == (ctas or nsm)
             out = p.reconstruct(xin)

@@ -64,7 +64,14 @@ def _geometries(synth):
     lgs = [i for i in range(9) if base["kind"][i] == 1]
     lgs_native = dict(base, dir_x=base["dir_x"][lgs], dir_y=base["dir_y"][lgs], kind=base["kind"][lgs],
                       output_metric=0)
-    return [("ngs-256-L9", ngs), ("tiny-ngs-32", tiny), ("lgs-64-native", lgs_native)]
+    # 512 grid with 16 stars: B (64 rows of 4 KB per column) is too large to stage in shared memory, the
+    # case where the persistent kernel could take two phase-2 columns per pass; the entry point lays out
+    # shared memory for the one-column kernel it launches.  Scratch: 16 * 256 * 64 * 8 B of row spectra
+    # and 4 * 256 * 512 * 8 B of layer spectra fit in 8 MiB.
+    az = np.deg2rad(22.5 * np.arange(16))
+    ngs512 = dict(synth.scaled(synth.config(3), M=512, P=64, L=4), precision="fp32",
+                  dir_x=2.9e-4 * np.cos(az), dir_y=2.9e-4 * np.sin(az), kind=np.zeros(16, np.int32))
+    return [("ngs-256-L9", ngs), ("tiny-ngs-32", tiny), ("lgs-64-native", lgs_native), ("ngs-512-L4-G16", ngs512)]
 
 
 @pytest.mark.gpu
