@@ -626,6 +626,20 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 if (!__any_sync(0xffffffffu, act)) continue;
                 const int tk = act ? task : 0, c = tk / G, ss = tk - c * G, k = kb + c * nb;
                 const C *src = fp.w1 + ((size_t)ss * Mh + k) * P;
+                const bool tt = fp.any_tt && act && s_star_tt[ss];
+                // the star's tip/tilt from the row shares of phase 1 (first pass: every column of the
+                // pass needs them): the first batch of shares is loaded together with the column, so
+                // the two L2 round trips overlap
+                const bool tt_sum = first && fp.any_tt;
+                R pb[QC], pc[QC];
+                auto load_shares = [&](int a0) {
+#pragma unroll
+                    for (int u = 0; u < QC; ++u) {
+                        const int a = a0 + t + LW * u;
+                        pb[u] = tt && a < P ? __ldcg(fp.pm + ((size_t)ss * P + a) * 2) : R(0);
+                        pc[u] = tt && a < P ? __ldcg(fp.pm + ((size_t)ss * P + a) * 2 + 1) : R(0);
+                    }
+                };
                 C v[RR];
                 if constexpr (M >= 512) {
                     // the column's P values go to this task's own row of Dp by asynchronous copies (the
@@ -638,6 +652,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                         const int pp = t + LW * r - o;
                         if (act && pp >= 0 && pp < P) cp_async_el(stg + pp, src + pp);
                     }
+                    if (tt_sum) load_shares(0);
                     cp_async_wait_all();
                     __syncwarp();
 #pragma unroll
@@ -648,31 +663,26 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                 } else {
 #pragma unroll
                     for (int r = 0; r < RR; ++r) v[r] = __ldcg(src + min(max(t + LW * r - o, 0), P - 1));
+                    if (tt_sum) load_shares(0);
 #pragma unroll
                     for (int r = 0; r < RR; ++r) {  // loads first (clamped addresses), then the zero extension
                         const int pp = t + LW * r - o;
                         if (!(act && pp >= 0 && pp < P)) v[r] = C{0, 0};
                     }
                 }
-                const bool tt = fp.any_tt && act && s_star_tt[ss];
                 R tb = 0, tc = 0;  // tip/tilt of the star
-                if (first && fp.any_tt) {  // from the row shares of phase 1 (every column of this pass)
+                if (tt_sum) {
                     R sb = 0, scs = 0;
-                    if (tt)
-                        for (int a0 = 0; a0 < P; a0 += LW * QC) {
-                            R pb[QC], pc[QC];
+                    for (int a0 = 0;;) {
 #pragma unroll
-                            for (int u = 0; u < QC; ++u) {
-                                const int a = a0 + t + LW * u;
-                                pb[u] = a < P ? __ldcg(fp.pm + ((size_t)ss * P + a) * 2) : R(0);
-                                pc[u] = a < P ? __ldcg(fp.pm + ((size_t)ss * P + a) * 2 + 1) : R(0);
-                            }
-#pragma unroll
-                            for (int u = 0; u < QC; ++u) {
-                                sb += pb[u];
-                                scs += pc[u];
-                            }
+                        for (int u = 0; u < QC; ++u) {
+                            sb += pb[u];
+                            scs += pc[u];
                         }
+                        a0 += LW * QC;
+                        if (a0 >= P) break;
+                        load_shares(a0);  // rows beyond the first batch (P > LW * QC)
+                    }
 #pragma unroll
                     for (int off = LW / 2; off > 0; off >>= 1) {
                         sb += __shfl_xor_sync(0xffffffffu, sb, off);
