@@ -262,7 +262,8 @@ def measure_workload(safr, synth, torch, dev, stream, k, steps, warmup, flush_l2
     out = {"grid": M, "pupil": info["P"], "stars": info["G"], "layers": info["L"], "precision": prec,
            "frames_per_s": 1e3 / mean_ms, "latency_ms": {"p50": lat[len(lat) // 2],
                                                          "p99": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]},
-           "path": "fused" if safr.safr_launches_per_frame(plan.handle) == 1 else "passes",
+           "path": {safr.SAFR_PATH_FUSED: "fused", safr.SAFR_PATH_PASSES: "passes",
+                    safr.SAFR_PATH_CLUSTER: "cluster"}[safr.safr_get_path(plan.handle)],
            "algorithmic_bytes": fbytes, "frac_of_hbm": fbytes / (mean_ms * 1e-3) / 1e9 / hbm,
            "rel_l2_vs_oracle": err, "rel_l2_per_layer_own": own, "rel_l2_per_layer_own_max": max(own),
            "compared": what, "steps": steps}
@@ -741,7 +742,27 @@ def run_safr(args):
     # (2) the same frames back to back on one plan: B stays in the L2 (warm)
     warm_ms, warm_host_s, warm_sleep_s = back_to_back(safr, torch, stream, [plan], frames, [layers], args.steps,
                                                       host_us)
-    # (3) per-frame latency, L2 flushed before every frame
+    # (3) the pool's frames as one batch graph per call (safr_batch_reconstruct): frames run
+    # concurrently on K chains of the graph, each on 1/K of the SMs (K timed at the first capture)
+    batch = safr.safr_batch_create([p.handle for p in pool])
+    xs_b = [frames[j % len(frames)] for j in range(len(pool))]
+    safr.safr_batch_reconstruct(batch, xs_b, outs, stream=stream)  # capture (times K)
+    torch.cuda.synchronize(dev)
+    n_calls = max(1, args.steps // len(pool))
+    for _ in range(3):
+        safr.safr_batch_reconstruct(batch, xs_b, outs, stream=stream)
+    torch.cuda.synchronize(dev)
+    bs, be = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bs.record(stream)
+    for _ in range(n_calls):
+        safr.safr_batch_reconstruct(batch, xs_b, outs, stream=stream)
+    be.record(stream)
+    be.synchronize()
+    conc_ms = bs.elapsed_time(be)
+    conc_chains = safr.safr_batch_chains(batch)
+    conc_status = safr.safr_batch_get_status(batch)
+    safr.safr_batch_destroy(batch)
+    # (4) per-frame latency, L2 flushed before every frame
     lat = latency_run(safr, torch, stream, plan, frames, layers, args.latency_frames, flush_l2)
     clk = clocks.stop()
     # per-kernel durations and in-kernel phase marks from separate traced frames
@@ -857,6 +878,12 @@ def run_safr(args):
                            "all_queued_before_gpu_start": cold_host_s < cold_sleep_s,
                            "how": f"{args.steps} frames back to back over {args.pool} plans of the workload "
                                   f"({args.pool} x 21 MB of B: every frame's B comes from HBM)"},
+                "concurrent_chains": {"frames_per_s": n_calls * len(pool) / (conc_ms * 1e-3),
+                                      "us_per_frame": 1e3 * conc_ms / (n_calls * len(pool)), "chains": conc_chains,
+                                      "device_status": conc_status,
+                                      "how": f"the {len(pool)} plans' frames as one safr_batch_reconstruct graph "
+                                             f"launch per call, {n_calls} calls back to back: the frames run "
+                                             f"{conc_chains} at a time, each on 1/{conc_chains} of the SMs"},
                 "warm_L2": {"frames_per_s": args.steps / (warm_ms * 1e-3), "us_per_frame": 1e6 * warm_s,
                             "host_submit_us_per_frame": 1e6 * warm_host_s / args.steps,
                             "all_queued_before_gpu_start": warm_host_s < warm_sleep_s,

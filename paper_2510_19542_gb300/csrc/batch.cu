@@ -137,16 +137,17 @@ bool capture_k(safr_batch_s *b, int K, const void *const *in, const float *const
     // capture and put back after it (the captured launches keep their own copies of the parameters)
     struct Saved {
         safr_plan_s *pl;
-        int grid, rt;
+        int grid, rt, pdl;
     };
     std::vector<Saved> saved;
     bool conf_ok = true;
     if (K > 1)
         for (safr_plan_s *pl : b->plans)
             if (concurrent_frame(pl) && safr::use_fused(pl)) {  // a one-cluster frame keeps its cluster
-                saved.push_back({pl, pl->f2_grid_force, pl->f2_rt_force});
+                saved.push_back({pl, pl->f2_grid_force, pl->f2_rt_force, pl->f2_pdl});
                 pl->f2_grid_force = nsm / K;
                 pl->f2_rt_force = pl->f2_rt3;
+                pl->f2_pdl = 0;  // no early CTAs holding SMs the other chains could use
                 conf_ok = conf_ok && safr::configure_fused(pl) && safr::use_fused(pl);
             }
     cudaGraph_t graph = nullptr;
@@ -196,6 +197,7 @@ bool capture_k(safr_batch_s *b, int K, const void *const *in, const float *const
     for (const Saved &v : saved) {
         v.pl->f2_grid_force = v.grid;
         v.pl->f2_rt_force = v.rt;
+        v.pl->f2_pdl = v.pdl;
         safr::configure_fused(v.pl);
     }
     cudaGetLastError();

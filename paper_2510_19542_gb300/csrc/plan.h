@@ -108,6 +108,7 @@ struct safr_plan_s {
     int f2_grid_force = 0;      // CTAs of the persistent kernel (0: one per SM)
     int f2_ck = 1;              // phase-2 columns per pass
     int f2_ck_allow = 1;        // 0: one column per pass (schedule choice)
+    int f2_pdl = 1;             // launch with programmatic stream serialization (0: plain launch)
     int autotuned = 0;          // 1 after safr_autotune
     // one-cluster kernel for grids up to 64 (cluster_impl.cuh)
     int cl_ok = 0;              // the one-cluster kernel fits this plan
