@@ -16,14 +16,19 @@
 // arithmetic FP32.  Its inputs are fixed per plan, so inference runs once,
 // when B is built, and the per-frame kernels are unchanged.
 //
-// Training (hand-written kernels, all on the GPU): frames of the SAFR forward
-// model in the Fourier domain, d_g(n) = sum_l e^{i theta_gl(n)} phi_l(n) +
-// eta_g(n), with von Karman layer spectra and white noise drawn from a
-// counter-based generator (Philox4x32-10, Salmon et al., SC 2011); the loss
-// is the relative squared error of the reconstructed layer spectra (Parseval:
-// the squared error of the layers); its gradient flows through the MLP;
-// Adam updates FP32 master weights.  Held-out frames compare the learned filter
-// against plain SAFR, which stays in the plan if it is not beaten.
+// Training (hand-written kernels, all on the GPU): frames of the layered model
+// of Section 2 through the aperture.  Layer spectra phi_l(n) are drawn with the
+// von Karman variance of a layer's DFT and made Hermitian (real screens); star
+// g's spectrum c_g(n) = sum_l e^{i theta_gl(n)} phi_l(n) is taken back to real
+// space, restricted to the plan's pupil (the operator A_g acts on the aperture
+// Omega_A), given white pixel noise with standard deviation noise level x the
+// RMS of the masked noise-free wavefront, and transformed again: d_g =
+// DFT2(psi_g).  All random numbers come from a counter-based generator
+// (Philox4x32-10, Salmon et al., SC 2011).  The loss is the relative squared
+// error of the reconstructed layer spectra (Parseval: the squared error of the
+// layers); its gradient flows through the MLP; Adam updates FP32 master
+// weights.  Held-out frames compare the learned filter against plain SAFR,
+// which stays in the plan if it is not beaten.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
