@@ -131,20 +131,31 @@ __device__ __forceinline__ C shfl_xor_c(C v, int m)
     return C{__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m)};
 }
 
+// Whether the last two lane stages (first two of the inverse) run without complex products.
+// Measured: 21.04 -> 20.20 us per back-to-back 256-grid frame (8 values per lane); at 16 values per
+// lane (the 512 grid) the peeled stages made the frame 4 us slower, so it keeps the plain loop.
+template <int M>
+__host__ __device__ constexpr bool wfft_peel() { return WShape<M>::R <= 8 && WShape<M>::LW >= 4; }
+
 // Forward transform, natural order in, permuted order out (see above).
+// Lane stage h multiplies the lower lane's difference by W_(2h)^(t mod h).  For h >= 4 that is a
+// general complex product; the last two stages need none: for h = 2 the factor is 1 or -i (a swap
+// with a sign), for h = 1 it is 1, so their chains carry one add per value instead of three
+// dependent operations.
 template <int M, typename C>
 __device__ __forceinline__ void wfft_fwd(C (&v)[WShape<M>::R], const WTw<M, C> &w, int t)
 {
     using S = WShape<M>;
+    using R = decltype(C{}.x);
+    constexpr int HLAST = wfft_peel<M>() ? 4 : 1;  // the general loop's last stage
     dft_reg<S::R, false>(v);
 #pragma unroll
     for (int k = 1; k < S::R; ++k) v[k] = c_mul(v[k], w.tw[k]);
     // stage h: W_(2h)^(t mod h) = W_LW^((t mod h) * LW / (2h))
 #pragma unroll 1
-    for (int h = S::LW / 2; h > 0; h >>= 1) {
+    for (int h = S::LW / 2; h >= HLAST; h >>= 1) {
         // upper lane: v + p; lower lane: (p - v) W.  As (sg v + p) wp with sg = -1, wp = W on the
         // lower lane and sg = 1, wp = 1 on the upper one.
-        using R = decltype(C{}.x);
         const bool low = (t & h) != 0;
         const C ws = w.wlw[(t & (h - 1)) * (S::LW / (2 * h))];
         const C wp = low ? ws : C{R(1), R(0)};
@@ -155,17 +166,58 @@ __device__ __forceinline__ void wfft_fwd(C (&v)[WShape<M>::R], const WTw<M, C> &
             v[k] = c_mul(C{sg * v[k].x + p.x, sg * v[k].y + p.y}, wp);
         }
     }
+    if constexpr (wfft_peel<M>()) {
+        {  // h = 2: the lower lanes with t odd multiply by -i: (x, y) -> (y, -x)
+            const bool low = (t & 2) != 0, rot = low && (t & 1);
+            const R sg = low ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < S::R; ++k) {
+                const C p = shfl_xor_c(v[k], 2);
+                const C u = C{sg * v[k].x + p.x, sg * v[k].y + p.y};
+                v[k] = rot ? C{u.y, -u.x} : u;
+            }
+        }
+        {  // h = 1: factor 1
+            const R sg = (t & 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < S::R; ++k) {
+                const C p = shfl_xor_c(v[k], 1);
+                v[k] = C{sg * v[k].x + p.x, sg * v[k].y + p.y};
+            }
+        }
+    }
 }
 
-// Inverse transform (unnormalised), permuted order in, natural order out.
+// Inverse transform (unnormalised), permuted order in, natural order out.  The first two lane
+// stages need no complex product (factor 1; then 1 or +i, a swap with a sign).
 template <int M, typename C>
 __device__ __forceinline__ void wfft_inv(C (&v)[WShape<M>::R], const WTw<M, C> &w, int t)
 {
     using S = WShape<M>;
+    using R = decltype(C{}.x);
+    if constexpr (wfft_peel<M>()) {
+        {  // h = 1: factor 1
+            const R sg = (t & 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < S::R; ++k) {
+                const C p = shfl_xor_c(v[k], 1);
+                v[k] = C{sg * v[k].x + p.x, sg * v[k].y + p.y};
+            }
+        }
+        {  // h = 2: the lower lanes with t odd multiply by +i: (x, y) -> (-y, x)
+            const bool low = (t & 2) != 0, rot = low && (t & 1);
+            const R sg = low ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < S::R; ++k) {
+                const C u = rot ? C{-v[k].y, v[k].x} : v[k];
+                const C p = shfl_xor_c(u, 2);
+                v[k] = C{sg * u.x + p.x, sg * u.y + p.y};
+            }
+        }
+    }
 #pragma unroll 1
-    for (int h = 1; h < S::LW; h <<= 1) {
+    for (int h = wfft_peel<M>() ? 4 : 1; h < S::LW; h <<= 1) {
         // lower lane: u = v conj(W), result p - u; upper lane: u = v, result u + p
-        using R = decltype(C{}.x);
         const bool low = (t & h) != 0;
         const C ws = w.wlw[(t & (h - 1)) * (S::LW / (2 * h))];
         const C wc = low ? C{ws.x, -ws.y} : C{R(1), R(0)};
@@ -188,9 +240,33 @@ template <int M, int N, typename C>
 __device__ __forceinline__ void wfft_inv_n(C (&v)[N][WShape<M>::R], const WTw<M, C> &w, int t)
 {
     using S = WShape<M>;
+    using R = decltype(C{}.x);
+    if constexpr (wfft_peel<M>()) {
+        {  // h = 1: factor 1
+            const R sg = (t & 1) ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < S::R; ++k)
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    const C p = shfl_xor_c(v[n][k], 1);
+                    v[n][k] = C{sg * v[n][k].x + p.x, sg * v[n][k].y + p.y};
+                }
+        }
+        {  // h = 2: +i on the lower lanes with t odd
+            const bool low = (t & 2) != 0, rot = low && (t & 1);
+            const R sg = low ? R(-1) : R(1);
+#pragma unroll
+            for (int k = 0; k < S::R; ++k)
+#pragma unroll
+                for (int n = 0; n < N; ++n) {
+                    const C u = rot ? C{-v[n][k].y, v[n][k].x} : v[n][k];
+                    const C p = shfl_xor_c(u, 2);
+                    v[n][k] = C{sg * u.x + p.x, sg * u.y + p.y};
+                }
+        }
+    }
 #pragma unroll 1
-    for (int h = 1; h < S::LW; h <<= 1) {
-        using R = decltype(C{}.x);
+    for (int h = wfft_peel<M>() ? 4 : 1; h < S::LW; h <<= 1) {
         const bool low = (t & h) != 0;
         const C ws = w.wlw[(t & (h - 1)) * (S::LW / (2 * h))];
         const C wc = low ? C{ws.x, -ws.y} : C{R(1), R(0)};
