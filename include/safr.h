@@ -173,6 +173,25 @@ safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const f
                              void *d_layers, float *d_out_scales, cudaStream_t stream);
 
 /*
+ * n frames of one plan (Algorithm 1 for each; the paper reconstructs one frame
+ * at a time and has no counterpart of the multi-frame launch).  The arrays are
+ * contiguous: d_wavefronts [n][G][P][P], d_layers [n][L][M][M], d_in_scales
+ * [n][G], d_out_scales [n][L] (FP16 storage), element types as for
+ * safr_reconstruct; frame f's layers are exactly those safr_reconstruct gives
+ * for frame f.  On the persistent kernel the n frames run in ONE launch, one
+ * after the other, each CTA starting the next frame as soon as it has finished
+ * the last phase of the previous one (no launch, no prologue wait between
+ * frames); the plan's workspaces serve every frame.  On the other schedules the
+ * frames are launched one by one, and every frame's buffers must then be
+ * 16-byte aligned (SAFR_ERR_MISALIGNED otherwise, nothing launched).  The base
+ * pointers must be 16-byte aligned device memory.  Asynchronous on `stream`,
+ * no allocation, no host synchronisation.  SAFR_ERR_INVALID_ARG for n < 1 or a
+ * NULL buffer; errors as safr_reconstruct otherwise.
+ */
+safr_status safr_reconstruct_frames(safr_plan_t plan, int n, const void *d_wavefronts, const float *d_in_scales,
+                                    void *d_layers, float *d_out_scales, cudaStream_t stream);
+
+/*
  * End-to-end form of safr_reconstruct for host buffers, synchronising
  * `stream` before returning.  When every buffer is page-locked, mapped host
  * memory (cudaHostAlloc, cudaHostRegister) aligned to 16 bytes, the kernels

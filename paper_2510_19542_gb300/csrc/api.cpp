@@ -490,6 +490,40 @@ safr_status safr_reconstruct(safr_plan_t plan, const void *d_wavefronts, const f
     return SAFR_OK;
 }
 
+safr_status safr_reconstruct_frames(safr_plan_t plan, int n, const void *d_wavefronts, const float *d_in_scales,
+                                    void *d_layers, float *d_out_scales, cudaStream_t stream)
+{
+    if (!plan || n < 1 || !d_wavefronts || !d_layers) return SAFR_ERR_INVALID_ARG;
+    if (!plan->precomputed) return SAFR_ERR_NOT_PRECOMPUTED;
+    if (plan->precision == SAFR_FP16_STORAGE && !d_out_scales) return SAFR_ERR_INVALID_ARG;
+    if (plan->precision != SAFR_FP16_STORAGE && (d_in_scales || d_out_scales)) return SAFR_ERR_INVALID_ARG;
+    if (!aligned16(d_wavefronts) || !aligned16(d_layers) || (d_in_scales && !aligned16(d_in_scales)) ||
+        (d_out_scales && !aligned16(d_out_scales)))
+        return SAFR_ERR_MISALIGNED;
+    const bool one_launch = safr::use_fused(plan) && plan->f2_frames_ok;
+    // frame by frame (other schedules): every frame's buffers must be aligned as safr_reconstruct's
+    if (!one_launch && n > 1 &&
+        (plan->in_bytes % 16 || plan->out_bytes % 16 || (d_in_scales && (plan->G * sizeof(float)) % 16) ||
+         (d_out_scales && (plan->L * sizeof(float)) % 16)))
+        return SAFR_ERR_MISALIGNED;
+    DeviceGuard guard(plan->device);
+    if (!guard.ok) return SAFR_ERR_CUDA;
+    if (one_launch) {
+        if (safr::launch_fused_frames(plan, d_wavefronts, d_in_scales, d_layers, d_out_scales, n, stream) !=
+            cudaSuccess)
+            return SAFR_ERR_CUDA;
+        return SAFR_OK;
+    }
+    for (int f = 0; f < n; ++f) {
+        const void *in = (const unsigned char *)d_wavefronts + (size_t)f * plan->in_bytes;
+        void *out = (unsigned char *)d_layers + (size_t)f * plan->out_bytes;
+        const float *isc = d_in_scales ? d_in_scales + (size_t)f * plan->G : nullptr;
+        float *osc = d_out_scales ? d_out_scales + (size_t)f * plan->L : nullptr;
+        if (dispatch(plan, in, isc, out, osc, stream) != cudaSuccess) return SAFR_ERR_CUDA;
+    }
+    return SAFR_OK;
+}
+
 // The device address of a page-locked, mapped host buffer (16-byte aligned), else null: the GPU
 // then reads and writes it directly over the host link (NVLink-C2C on Grace) without staging copies.
 const void *host_alias(const void *h)

@@ -9,4 +9,9 @@ cudaError_t frame2_launch_f16(safr_plan_s *pl, const void *in, const float *isc,
 {
     return Frame2F16::launch(pl, in, isc, out, osc, st);
 }
+cudaError_t frame2_launch_frames_f16(safr_plan_s *pl, const void *in, const float *isc, void *out, float *osc, int n,
+                                     cudaStream_t st)
+{
+    return Frame2F16::launch_frames(pl, in, isc, out, osc, n, st);
+}
 }  // namespace safr

@@ -10,4 +10,9 @@ cudaError_t frame2_launch_f64(safr_plan_s *pl, const void *in, const float *isc,
 {
     return Frame2F64::launch(pl, in, isc, out, osc, st);
 }
+cudaError_t frame2_launch_frames_f64(safr_plan_s *pl, const void *in, const float *isc, void *out, float *osc, int n,
+                                     cudaStream_t st)
+{
+    return Frame2F64::launch_frames(pl, in, isc, out, osc, n, st);
+}
 }  // namespace safr

@@ -297,14 +297,16 @@ __device__ __forceinline__ unsigned long long bar_count_read(const unsigned long
     return threadIdx.x == 0 ? __ldcg(bar + 1) : 0ull;
 }
 // One frame of Algorithm 1 on the whole grid (all CTAs call it together).
-//   bar_base   set to the arrivals counted on fp.bar before this frame (thread 0), read once the
-//              kernels before this one in the stream have finished
+//   bar_base   the arrivals counted on fp.bar before this frame (thread 0); the first frame of the
+//              launch reads it once the kernels before this one in the stream have finished
 //   bph, tph   parities of the B and table mbarriers for this frame's first waits
 //   first      the first frame of the launch: initialises the mbarriers
+//   fidx       frame index within the launch: its wavefronts, layers and scales are the fidx-th of
+//              contiguous arrays (fp.in + fidx G P^2, fp.out + fidx L M^2, G and L scales per frame)
 // Returns false if a bounded wait gave up (status recorded); the caller then stops.
 template <int M, typename R, typename TIN, typename TOUT, int CKT>
 __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned long long &bar_base, unsigned &bph,
-                                           unsigned tph, bool first_frame)
+                                           unsigned tph, bool first_frame, int fidx = 0)
 {
     using C = typename Frame2Params<R>::C;
     using S = WShape<M>;
@@ -430,8 +432,10 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     // launched right after another one starts while that one finishes (programmatic dependent
     // launch); its inputs, the workspaces and the barrier counter are touched only after the
     // kernels before it in the stream have finished and their writes are visible.
-    pdl_wait();
-    bar_base = bar_count_read(fp.bar);
+    if (first_frame) {
+        pdl_wait();
+        bar_base = bar_count_read(fp.bar);
+    }
     __syncthreads();  // the parameter copies
     SAFR_MARK(1, true);
 
@@ -460,8 +464,8 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             if (!__any_sync(0xffffffffu, act)) continue;  // a warp with no transform in this round stays idle
             const int item = act ? i : lo, g = item / fp.npr, a0 = 2 * (item - g * fp.npr);
             const bool has1 = a0 + 1 < P;
-            const TIN *psi = (const TIN *)fp.in + (size_t)g * P * P;
-            const R sc = fp.in_scales ? (R)fp.in_scales[g] : R(1);
+            const TIN *psi = (const TIN *)fp.in + ((size_t)fidx * G + g) * P * P;
+            const R sc = fp.in_scales ? (R)fp.in_scales[(size_t)fidx * G + g] : R(1);
             const bool tt = act && fp.any_tt && s_star_tt[g];
             // z[q] = psi[a0][q - o] + i psi[a0 + 1][q - o]: lane t holds q = t + LW r.
             // All loads (the two rows and, for removeTT, their pupil-mask words) are issued
@@ -995,11 +999,11 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                     sc = ldexpf(1.0f, f < 0.70710678f ? ex - 1 : ex);
                 }
                 inv_scale = (R)(1.0f / sc);
-                if (p0 == 0 && tid == 0) fp.out_scales[l] = sc;
+                if (p0 == 0 && tid == 0) fp.out_scales[(size_t)fidx * L + l] = sc;
             }
             // output row r of a group is Z[r / 2] of that group (real part for even r, imaginary for odd)
             const R f = fp.inv_M2 * inv_scale;
-            TOUT *outp = (TOUT *)fp.out + ((size_t)l * M + p0) * M;
+            TOUT *outp = (TOUT *)fp.out + (((size_t)fidx * L + l) * M + p0) * M;
             for (int idx = tid; idx < nr * M; idx += NTH) {
                 const int r = idx >> LOGM, q = idx & (M - 1);
                 const C *zr = Z + (size_t)(r >> 1) * M;
@@ -1052,6 +1056,27 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
     unsigned bph = 0;
     if (frame_body<M, R, TIN, TOUT, CK>(fp, base, bph, 0u, true))
         bar_count_advance(fp.bar, base, 2ull * gridDim.x);
+}
+
+// `nframes` frames of one plan in one launch, one after the other (contiguous input and output
+// arrays).  Each frame is the same sequence of three phases and two grid barriers; between frames
+// there is no launch and no prologue wait: a CTA that finished frame f's last phase starts frame
+// f + 1's first at once.  The workspaces need no second copy.  Frame f + 1 writes the row spectra
+// after frame f's second grid barrier, which a CTA passes only once every CTA is done with frame f's
+// column phase, their only reader; it writes the layer spectra after its own first grid barrier,
+// which a CTA passes only once every CTA is done with frame f's last phase, their only reader.
+template <int M, typename R, typename TIN, typename TOUT, int CK = 1>
+__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2_frames(Frame2Params<R> fp, int nframes)
+{
+    pdl_trigger();
+    unsigned long long base = 0;
+    unsigned bph = 0;
+    for (int f = 0; f < nframes; ++f) {
+        unsigned long long bf = base + 2ull * gridDim.x * (unsigned long long)f;  // frame 0 reads it
+        if (!frame_body<M, R, TIN, TOUT, CK>(fp, bf, bph, (unsigned)(f & 1), f == 0, f)) return;
+        if (f == 0) base = bf;
+    }
+    bar_count_advance(fp.bar, base, 2ull * gridDim.x * (unsigned long long)nframes);
 }
 
 // ----------------------------------------------------------------------------

@@ -109,6 +109,7 @@ struct safr_plan_s {
     int f2_ck = 1;              // phase-2 columns per pass
     int f2_ck_allow = 1;        // 0: one column per pass (schedule choice)
     int f2_pdl = 1;             // launch with programmatic stream serialization (0: plain launch)
+    int f2_frames_ok = 0;       // the several-frames instance has its shared-memory limit raised
     int autotuned = 0;          // 1 after safr_autotune
     // one-cluster kernel for grids up to 64 (cluster_impl.cuh)
     int cl_ok = 0;              // the one-cluster kernel fits this plan
@@ -171,6 +172,8 @@ int launches_per_frame(const safr_plan_s *plan);
 bool configure_fused(safr_plan_s *plan);
 cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scales, void *out, float *out_scales,
                          cudaStream_t stream);
+cudaError_t launch_fused_frames(safr_plan_s *plan, const void *in, const float *in_scales, void *out,
+                                float *out_scales, int n, cudaStream_t stream);
 void frame2_twiddles(int M, std::vector<double> &re, std::vector<double> &im);
 void filter_free(safr_plan_s *plan);
 void filter_invalidate(safr_plan_s *plan);  // the SVD basis is stale (the geometry changed)

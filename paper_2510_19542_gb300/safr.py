@@ -41,7 +41,7 @@ _EXPORTS = ["safr_plan_create", "safr_precompute", "safr_reconstruct", "safr_rec
             "safr_batch_destroy", "safr_batch_graph", "safr_filter_train", "safr_filter_apply",
             "safr_filter_reset", "safr_polc", "safr_integrate", "safr_loop_step", "safr_refresh",
             "safr_plan_save", "safr_plan_load", "safr_trace_stamps", "safr_set_grid", "safr_get_grid",
-            "safr_batch_chains", "safr_set_tile_rows", "safr_batch_set_chains"]
+            "safr_batch_chains", "safr_set_tile_rows", "safr_batch_set_chains", "safr_reconstruct_frames"]
 SAFR_NOALLOC_SCRATCH_BYTES = 8 << 20
 SAFR_FILTER_PARAMS = 8705
 
@@ -108,6 +108,7 @@ def load(build_if_missing: bool = True):
     lib.safr_precompute.argtypes = [vp, vp]
     lib.safr_reconstruct.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.safr_reconstruct_host.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.safr_reconstruct_frames.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
     lib.safr_get_status.argtypes = [vp]
     lib.safr_get_plan_info.argtypes = [vp, C.POINTER(safr_plan_info)]
     lib.safr_copy_B.argtypes = [vp, C.c_int, vp]
@@ -228,6 +229,12 @@ def safr_precompute(plan: int, stream=None):
 def safr_reconstruct(plan: int, wavefronts, layers, in_scales=None, out_scales=None, stream=None):
     _check(load().safr_reconstruct(plan, _ptr(wavefronts), _ptr(in_scales), _ptr(layers), _ptr(out_scales),
                                    _stream(stream)), "safr_reconstruct")
+
+
+def safr_reconstruct_frames(plan: int, n: int, wavefronts, layers, in_scales=None, out_scales=None, stream=None):
+    """n frames of one plan; contiguous [n][G][P][P] wavefronts, [n][L][M][M] layers."""
+    _check(load().safr_reconstruct_frames(plan, int(n), _ptr(wavefronts), _ptr(in_scales), _ptr(layers),
+                                          _ptr(out_scales), _stream(stream)), "safr_reconstruct_frames")
 
 
 def safr_reconstruct_host(plan: int, wavefronts, layers, in_scales=None, out_scales=None, stream=None):
