@@ -140,6 +140,12 @@ typedef struct {
  * (c_l delta) and the resample tables, and allocate B and the workspaces on
  * `cuda_device`.  On success *out is a new plan; on failure *out is NULL and
  * nothing stays allocated.  A mixed plan with SAFR_NATIVE output is rejected.
+ * Besides the limits above, the three-pass kernels, which every plan keeps as
+ * its fallback schedule, must fit in one SM's shared memory: their column pass
+ * holds (3 Gmax + 1) M complex values (Gmax = stars in the larger group), so at
+ * M = 1024 a group may have at most 9 stars in FP32 and 4 in FP64, and the
+ * resampling pass of a mixed FP64 plan does not fit at M = 1024.  Such a shape
+ * returns SAFR_ERR_UNSUPPORTED_SIZE.
  */
 safr_status safr_plan_create(const safr_geometry *geom, int cuda_device, safr_plan_t *out);
 

@@ -53,6 +53,14 @@ def _geom(**kw):
 @pytest.mark.parametrize("change,status", [
     (dict(M=48), 2),                       # not a power of two
     (dict(M=2048, P=20), 2),               # above the maximum grid
+    (dict(M=4, P=4), 2),                   # below the minimum grid
+    (dict(h=np.linspace(0, 16000.0, 65), cn2=np.full(65, 1 / 65)), 2),  # SAFR_MAX_L + 1 layers
+    (dict(dir_x=np.linspace(-5e-4, 5e-4, 33), dir_y=np.zeros(33),       # SAFR_MAX_G + 1 stars
+          kind=np.array([1] * 16 + [0] * 17, np.int32)), 2),
+    (dict(dir_x=np.linspace(-5e-4, 5e-4, 20), dir_y=np.zeros(20),       # 17 LGS in one group
+          kind=np.array([1] * 17 + [0] * 3, np.int32)), 2),
+    (dict(dir_x=np.linspace(-5e-4, 5e-4, 17), dir_y=np.zeros(17),       # 17 NGS in one group
+          kind=np.zeros(17, np.int32), output_metric=0), 2),
     (dict(P=65), 1),                       # pupil larger than the grid
     (dict(pitch=0.0), 1),
     (dict(alpha=0.0), 1),
