@@ -413,10 +413,8 @@ safr_status build_plan(const safr_geometry *g, safr_plan_s *p)
     SAFR_TRY(cudaMalloc((void **)&p->d_in_scales_stage, (size_t)p->G * sizeof(float)));
     SAFR_TRY(cudaMalloc((void **)&p->d_out_scales_stage, (size_t)L * sizeof(float)));
 
-    e = safr::configure_frame_kernels(p);
-    if (e != cudaSuccess) return SAFR_ERR_CUDA;
-    if (p->smem_k1 > 227 * 1024 || p->smem_k2 > 227 * 1024 || p->smem_k3 > 227 * 1024)
-        return SAFR_ERR_UNSUPPORTED_SIZE;
+    const safr_status ks = safr::configure_frame_kernels(p);
+    if (ks != SAFR_OK) return ks;
     p->fused_ok = safr::configure_fused(p) ? 1 : 0;
     cudaGetLastError();
     p->cl_ok = safr::configure_cluster(p) ? 1 : 0;

@@ -9,8 +9,9 @@ namespace safr {
 // The dynamic shared-memory limit of a kernel is a property of the kernel, shared
 // by every plan that launches it.  Raise it once to everything the device allows
 // next to the kernel's static shared memory (never lower it: a later plan with a
-// smaller need must not break an earlier one), and report whether `need` fits.
-inline bool smem_limit_allows(const void *kernel, size_t need)
+// smaller need must not break an earlier one), and report whether `need` fits:
+// 1 it fits, 0 it is more than the device allows, -1 a CUDA call failed.
+inline int smem_fit(const void *kernel, size_t need)
 {
     int dev = 0, optin = 0;
     cudaFuncAttributes fa;
@@ -18,17 +19,19 @@ inline bool smem_limit_allows(const void *kernel, size_t need)
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
         cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return -1;
     }
     const int avail = optin - (int)fa.sharedSizeBytes;
-    if (need > (size_t)avail) return false;
+    if (need > (size_t)avail) return 0;
     if (fa.maxDynamicSharedSizeBytes < avail &&
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, avail) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return -1;
     }
-    return true;
+    return 1;
 }
+
+inline bool smem_limit_allows(const void *kernel, size_t need) { return smem_fit(kernel, need) == 1; }
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

@@ -167,7 +167,7 @@ namespace safr {
 cudaError_t launch_precompute(safr_plan_s *plan, cudaStream_t stream);
 cudaError_t launch_frame(safr_plan_s *plan, const void *in, const float *in_scales, void *out,
                          float *out_scales, cudaStream_t stream);
-cudaError_t configure_frame_kernels(safr_plan_s *plan);
+safr_status configure_frame_kernels(safr_plan_s *plan);
 int launches_per_frame(const safr_plan_s *plan);
 bool configure_fused(safr_plan_s *plan);
 cudaError_t launch_fused(safr_plan_s *plan, const void *in, const float *in_scales, void *out, float *out_scales,

@@ -397,16 +397,20 @@ static void (*cols_kernel(int gmax))(FrameParams<R>)
 }
 
 template <typename K1, typename K2, typename K3>
-static cudaError_t set_smem(K1 k1, K2 k2, K3 k3, const safr_plan_s *pl)
+static safr_status set_smem(K1 k1, K2 k2, K3 k3, const safr_plan_s *pl)
 {
-    const bool ok = smem_limit_allows((const void *)k1, pl->smem_k1) && smem_limit_allows((const void *)k2, pl->smem_k2) &&
-                    smem_limit_allows((const void *)k3, pl->smem_k3);
-    cudaError_t e = ok ? cudaSuccess : cudaErrorInvalidValue;
-    return e;
+    const int f[3] = {smem_fit((const void *)k1, pl->smem_k1), smem_fit((const void *)k2, pl->smem_k2),
+                      smem_fit((const void *)k3, pl->smem_k3)};
+    for (int i = 0; i < 3; ++i)
+        if (f[i] < 0) return SAFR_ERR_CUDA;
+    for (int i = 0; i < 3; ++i)
+        if (f[i] == 0) return SAFR_ERR_UNSUPPORTED_SIZE;
+    return SAFR_OK;
 }
 
-// Shared-memory sizes and launch shapes; called once at plan creation.
-cudaError_t configure_frame_kernels(safr_plan_s *pl)
+// Shared-memory sizes and launch shapes; called once at plan creation.  SAFR_ERR_UNSUPPORTED_SIZE
+// when a pass needs more shared memory than one CTA may have, SAFR_ERR_CUDA when a query failed.
+safr_status configure_frame_kernels(safr_plan_s *pl)
 {
     const int M = pl->M;
     const size_t cs = csize(pl), rs = rsize(pl);
