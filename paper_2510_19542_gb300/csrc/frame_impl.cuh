@@ -877,26 +877,43 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                     }
                 }
             }
+            // the power-of-two output scale of an FP16 layer (1 otherwise)
+            auto out_scale = [&]() -> R {
+                R inv_scale = R(1);
+                if constexpr (std::is_same<TOUT, __half>::value) {
+                    // layer energy sum_n |b(n)|^2 over the groups (fixed order) -> RMS = sqrt(energy) / M^2;
+                    // scale = 2^round(log2 RMS): 2^(e-1) for RMS = f 2^e, f in [1/2, 1), rounded at f = 2^-1/2
+                    R e = 0;
+                    for (int gi = 0; gi < fp.ngroups; ++gi)
+                        for (int k = tid; k < Mh; k += NTH) e += (R)__ldcg(fp.energy + ((size_t)gi * L + l) * Mh + k);
+                    e = block_sum(e, red);
+                    const float rms = sqrtf((float)e) / ((float)M * (float)M);
+                    float sc = 1.0f;
+                    if (rms > 0.0f && rms < INFINITY) {
+                        int ex;
+                        const float f = frexpf(rms, &ex);
+                        sc = ldexpf(1.0f, f < 0.70710678f ? ex - 1 : ex);
+                    }
+                    inv_scale = (R)(1.0f / sc);
+                    if (p0 == 0 && tid == 0) fp.out_scales[(size_t)fidx * L + l] = sc;
+                }
+                return inv_scale;
+            };
+            R inv_scale = R(1);
+            if constexpr (M < 512) inv_scale = out_scale();  // while the staging copies are in flight
             cp_async_wait_all();
             __syncthreads();
             SAFR_MARK(18, it == b);
-            // one inverse transform per output row pair r = 2i, 2i + 1 of each group:
-            // Z[k] = X1[k] + i X2[k] over the full length M from the stored half spectra,
-            // built directly in the permuted order.  An LGS row's spectrum is the
+            // The spectrum of output row pair r = 2i, 2i + 1 of a group, ready for its inverse
+            // transform: Z[k] = X1[k] + i X2[k] over the full length M from the stored half
+            // spectra, built directly in the permuted order.  An LGS row's spectrum is the
             // combination (1 - f) S[s] + f S[s + 1] of its two staged source rows.
-            for (int u0 = 0; u0 < ntot; u0 += UNITS) {
-                const int task = u0 + unit;
-                const bool act = task < ntot;
-                if (!__any_sync(0xffffffffu, act)) continue;
-                const int tk = act ? task : 0;  // an idle slot reads row pair 0 of group 0 (always staged)
-                const bool g1 = tk >= npair;
-                const int i = g1 ? tk - npair : tk;
+            auto build_v = [&](bool g1, int i, bool act, C(&v)[RR]) {
                 const C *sg = g1 ? stg1 : stg0;
                 const int st = g1 ? st1 : st0;
                 const bool hasb = 2 * i + 1 < nr;
                 // frequency k < M/2 reads stored column k; k > M/2 reads column M - k (conjugate
                 // symmetry); every lane loads from a valid address first, then selects
-                C v[RR];
                 constexpr int RB = RR < 8 ? RR : 8;  // values loaded per batch (bounds the registers at large M)
                 if (!g1 && rs0) {  // warp-uniform: the LGS group's rows, resampled along p
                     const int ra = p0 + 2 * i, rb = hasb ? ra + 1 : ra;
@@ -955,79 +972,140 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                         }
                     }
                 }
-                wfft_inv<M>(v, tw, t);
-                if (act)
-#pragma unroll
-                    for (int r = 0; r < RR; ++r) Z[(size_t)task * M + t + LW * r] = v[r];
-            }
-            SAFR_MARK(19, it == b);
-            __syncthreads();
-            SAFR_MARK(20, it == b);
-            if constexpr (M >= 512) {  // the next item's rows, while this one stores (no resample: rows p0..)
-                staged_ahead = false;
-                const int itn = it + nb;
-                if (!rs0 && itn < fp.n3) {
-                    const int ln = itn / fp.tiles3, p0n = (itn - ln * fp.tiles3) * RT, nrn = min(RT, M - p0n);
-                    const int ns1 = two ? nrn : 0;
-                    const C *src0 = fp.w2 + (size_t)ln * Mh * M;
-                    const C *src1 = fp.w2 + ((size_t)L + ln) * Mh * M;
-                    for (int s = lane; s < nrn || s < ns1; s += 32) {
-#pragma unroll 4
-                        for (int u = 0; u < KW; ++u) {
-                            const int k = warp + NW * u;
-                            const int sk = ((k / RR) >> 1) & 15;
-                            if (k < Mh && s < nrn) cp_async_el(stg0 + k * st0 + sk + s, src0 + ((size_t)k << LOGM) + p0n + s);
-                            if (k < Mh && s < ns1) cp_async_el(stg1 + k * st1 + sk + s, src1 + ((size_t)k << LOGM) + p0n + s);
-                        }
-                    }
-                    staged_ahead = true;
-                }
-            }
-            R inv_scale = R(1);
-            if constexpr (std::is_same<TOUT, __half>::value) {
-                // layer energy sum_n |b(n)|^2 over the groups (fixed order) -> RMS = sqrt(energy) / M^2;
-                // scale = 2^round(log2 RMS): 2^(e-1) for RMS = f 2^e, f in [1/2, 1), rounded at f = 2^-1/2
-                R e = 0;
-                for (int gi = 0; gi < fp.ngroups; ++gi)
-                    for (int k = tid; k < Mh; k += NTH) e += (R)__ldcg(fp.energy + ((size_t)gi * L + l) * Mh + k);
-                e = block_sum(e, red);
-                const float rms = sqrtf((float)e) / ((float)M * (float)M);
-                float sc = 1.0f;
-                if (rms > 0.0f && rms < INFINITY) {
-                    int ex;
-                    const float f = frexpf(rms, &ex);
-                    sc = ldexpf(1.0f, f < 0.70710678f ? ex - 1 : ex);
-                }
-                inv_scale = (R)(1.0f / sc);
-                if (p0 == 0 && tid == 0) fp.out_scales[(size_t)fidx * L + l] = sc;
-            }
-            // output row r of a group is Z[r / 2] of that group (real part for even r, imaginary for odd)
+            };
             const R f = fp.inv_M2 * inv_scale;
             TOUT *outp = (TOUT *)fp.out + (((size_t)fidx * L + l) * M + p0) * M;
-            for (int idx = tid; idx < nr * M; idx += NTH) {
-                const int r = idx >> LOGM, q = idx & (M - 1);
-                const C *zr = Z + (size_t)(r >> 1) * M;
-                R v;
-                if (rs0) {  // the column half of the bilinear resample (the row half was taken on the spectra)
-                    const R fv = tfw[q];
-                    const int j0u = ti0[q];
-                    const int ja = j0u & (M - 1), jb = (j0u + 1) & (M - 1);
-                    const R a0 = (r & 1) ? zr[ja].y : zr[ja].x, a1 = (r & 1) ? zr[jb].y : zr[jb].x;
-                    v = (R(1) - fv) * a0 + fv * a1;
-                } else {
-                    v = (r & 1) ? zr[q].y : zr[q].x;
-                }
-                if (two) {  // the NGS group's rows follow group 0's pairs
-                    const C zz = Z[(size_t)(npair + (r >> 1)) * M + q];
-                    v += (r & 1) ? zz.y : zz.x;
-                }
-                R val = v * f;
+            auto put = [&](TOUT *dst, R val) {
                 if constexpr (!std::is_same<TOUT, __half>::value)
-                    if (fp.blend) val = (R(1) - fp.gain) * (R)outp[idx] + fp.gain * val;
+                    if (fp.blend) val = (R(1) - fp.gain) * (R)*dst + fp.gain * val;
                 if constexpr (std::is_same<TOUT, double>::value)
-                    store_out_d(outp + idx, (double)val);
+                    store_out_d(dst, (double)val);
                 else
-                    store_out<TOUT>(outp + idx, (float)val);
+                    store_out<TOUT>(dst, (float)val);
+            };
+            if constexpr (M < 512) {
+                // Units in pairs: with two groups, units 2m and 2m + 1 take row pair i of group 0 and
+                // of group 1.  The group-0 unit leaves its rows in Z (row i); the group-1 unit, once the
+                // pair has met at a barrier of its own (a named barrier of two warps, or the warp), adds
+                // them (resampled along q for an LGS group) to its own rows and stores output rows 2i
+                // and 2i + 1.  With one group every unit stores its own row pair (through Z when it is
+                // resampled along q).  No block barrier separates the transforms from the stores.
+                const int PR = two ? UNITS / 2 : UNITS;  // row pairs per round
+                for (int i0 = 0; i0 < npair; i0 += PR) {
+                    const int i = i0 + (two ? unit >> 1 : unit);
+                    const bool act = i < npair;
+                    if (!__any_sync(0xffffffffu, act)) continue;  // the same for both units of a pair
+                    const bool g1 = two && (unit & 1);
+                    const int ii = act ? i : 0;  // an idle unit reads row pair 0 (always staged)
+                    C v[RR];
+                    build_v(g1, ii, act, v);
+                    wfft_inv<M>(v, tw, t);
+                    C *zr = Z + (size_t)ii * M;
+                    const bool storer = g1 || !two;
+                    if (act && (two ? !storer : rs0))  // group 0's rows, or a resampled single group's own
+#pragma unroll
+                        for (int r = 0; r < RR; ++r) zr[t + LW * r] = v[r];
+                    if (two) {
+                        if constexpr (S::TPW == 1)
+                            asm volatile("bar.sync %0, 64;" ::"r"(8 + (warp >> 1)) : "memory");
+                        else
+                            __syncwarp();
+                    } else if (rs0) {
+                        __syncwarp();
+                    }
+                    if (storer && act) {
+                        // output row 2i is the real part, row 2i + 1 the imaginary part
+                        TOUT *oa = outp + (size_t)(2 * ii) * M;
+                        const bool hasb = 2 * ii + 1 < nr;
+#pragma unroll
+                        for (int r = 0; r < RR; ++r) {
+                            const int q = t + LW * r;
+                            R e, od;
+                            if (rs0) {  // the column half of the bilinear resample (the row half was taken on the spectra)
+                                const R fv = tfw[q];
+                                const int j0u = ti0[q];
+                                const C za = zr[j0u & (M - 1)], zb = zr[(j0u + 1) & (M - 1)];
+                                e = (R(1) - fv) * za.x + fv * zb.x;
+                                od = (R(1) - fv) * za.y + fv * zb.y;
+                            } else if (two) {
+                                const C z = zr[q];
+                                e = z.x;
+                                od = z.y;
+                            } else {
+                                e = v[r].x;
+                                od = v[r].y;
+                            }
+                            if (two) {  // the NGS group's rows
+                                e += v[r].x;
+                                od += v[r].y;
+                            }
+                            put(oa + q, e * f);
+                            if (hasb) put(oa + M + q, od * f);
+                        }
+                    }
+                }
+                SAFR_MARK(19, it == b);
+                SAFR_MARK(20, it == b);
+            } else {
+                for (int u0 = 0; u0 < ntot; u0 += UNITS) {
+                    const int task = u0 + unit;
+                    const bool act = task < ntot;
+                    if (!__any_sync(0xffffffffu, act)) continue;
+                    const int tk = act ? task : 0;  // an idle slot reads row pair 0 of group 0 (always staged)
+                    const bool g1 = tk >= npair;
+                    const int i = g1 ? tk - npair : tk;
+                    C v[RR];
+                    build_v(g1, i, act, v);
+                    wfft_inv<M>(v, tw, t);
+                    if (act)
+#pragma unroll
+                        for (int r = 0; r < RR; ++r) Z[(size_t)task * M + t + LW * r] = v[r];
+                }
+                SAFR_MARK(19, it == b);
+                __syncthreads();
+                SAFR_MARK(20, it == b);
+                {  // the next item's rows, while this one stores (no resample: rows p0..)
+                    staged_ahead = false;
+                    const int itn = it + nb;
+                    if (!rs0 && itn < fp.n3) {
+                        const int ln = itn / fp.tiles3, p0n = (itn - ln * fp.tiles3) * RT, nrn = min(RT, M - p0n);
+                        const int ns1 = two ? nrn : 0;
+                        const C *src0 = fp.w2 + (size_t)ln * Mh * M;
+                        const C *src1 = fp.w2 + ((size_t)L + ln) * Mh * M;
+                        for (int s = lane; s < nrn || s < ns1; s += 32) {
+#pragma unroll 4
+                            for (int u = 0; u < KW; ++u) {
+                                const int k = warp + NW * u;
+                                const int sk = ((k / RR) >> 1) & 15;
+                                if (k < Mh && s < nrn) cp_async_el(stg0 + k * st0 + sk + s, src0 + ((size_t)k << LOGM) + p0n + s);
+                                if (k < Mh && s < ns1) cp_async_el(stg1 + k * st1 + sk + s, src1 + ((size_t)k << LOGM) + p0n + s);
+                            }
+                        }
+                        staged_ahead = true;
+                    }
+                }
+                inv_scale = out_scale();
+                const R f3 = fp.inv_M2 * inv_scale;
+                // output row r of a group is Z[r / 2] of that group (real part for even r, imaginary for odd)
+                for (int idx = tid; idx < nr * M; idx += NTH) {
+                    const int r = idx >> LOGM, q = idx & (M - 1);
+                    const C *zr = Z + (size_t)(r >> 1) * M;
+                    R v;
+                    if (rs0) {  // the column half of the bilinear resample (the row half was taken on the spectra)
+                        const R fv = tfw[q];
+                        const int j0u = ti0[q];
+                        const int ja = j0u & (M - 1), jb = (j0u + 1) & (M - 1);
+                        const R a0 = (r & 1) ? zr[ja].y : zr[ja].x, a1 = (r & 1) ? zr[jb].y : zr[jb].x;
+                        v = (R(1) - fv) * a0 + fv * a1;
+                    } else {
+                        v = (r & 1) ? zr[q].y : zr[q].x;
+                    }
+                    if (two) {  // the NGS group's rows follow group 0's pairs
+                        const C zz = Z[(size_t)(npair + (r >> 1)) * M + q];
+                        v += (r & 1) ? zz.y : zz.x;
+                    }
+                    put(outp + idx, v * f3);
+                }
             }
             __syncthreads();
             SAFR_MARK(21, it == b);
