@@ -438,7 +438,9 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
 
     // ---- phase 1: row pairs ----------------------------------------------------
     {
-        const int lo = (int)(((long long)b * fp.n1) / nb), hi = (int)(((long long)(b + 1) * fp.n1) / nb);
+        // 32-bit products: the grid is at most the SM count and n1 = G ceil(P / 2) <= 32 * 512, so
+        // (b + 1) n1 < 2^31 (a 64-bit division here cost 0.2 us per frame in code fetch)
+        const int lo = (b * fp.n1) / nb, hi = ((b + 1) * fp.n1) / nb;
         bool first = true;
         for (int base = lo; base < hi; base += UNITS) {
             const int i = base + unit;
