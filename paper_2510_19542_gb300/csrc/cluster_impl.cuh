@@ -147,7 +147,7 @@ __device__ __forceinline__ void cluster_barrier()
 __host__ __device__ constexpr int cluster_threads() { return 512; }
 
 template <int M, typename R, typename TIN, typename TOUT>
-__global__ void __launch_bounds__(cluster_threads(), 1) k_cluster(ClusterParams<R> cp)
+__global__ void __launch_bounds__(cluster_threads(), 1) k_cluster(const __grid_constant__ ClusterParams<R> cp)
 {
     using C = typename ClusterParams<R>::C;
     using S = WShape<M>;
@@ -228,22 +228,13 @@ __global__ void __launch_bounds__(cluster_threads(), 1) k_cluster(ClusterParams<
             }
         }
         if (stamp) stamp[13] = gtimer();
-    } else if (warp == 2) {
-#pragma unroll
-        for (int i = 0; i < SAFR_MAX_G; ++i)
-            if (lane == (i & 31)) s_star_tt[i] = cp.star_tt[i];
+    } else if (warp == 2) {  // the __grid_constant__ parameter read in place: one round of loads
+        for (int i = lane; i < SAFR_MAX_G; i += 32) s_star_tt[i] = cp.star_tt[i];
     } else if (warp == 3) {
-#pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-            if (lane == 0) {
-                s_grp[gi].G = cp.grp[gi].G;
-                s_grp[gi].b_row0 = cp.grp[gi].b_row0;
-                s_grp[gi].resample = cp.grp[gi].resample;
-            }
-#pragma unroll
-            for (int q = 0; q < SAFR_MAX_GROUP_G; ++q)
-                if (lane == q) s_grp[gi].star[q] = cp.grp[gi].star[q];
-        }
+        const int *src = reinterpret_cast<const int *>(&cp.grp[0]);
+        int *dst = reinterpret_cast<int *>(&s_grp[0]);
+        constexpr int NWD = (int)(2 * sizeof(GroupDev) / sizeof(int));
+        for (int i = lane; i < NWD; i += 32) dst[i] = src[i];
     }
     if (!cp.stage_b)  // this CTA's B columns, into L2 while phase 1 runs
         for (int q = 0; q < cp.ncol; ++q) {

@@ -316,23 +316,18 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     const int t = lane & (LW - 1);                             // lane within the transform
     const int unit = warp * S::TPW + (lane >> LB);             // transform slot of this lane
     const int bt = LB > 0 ? (int)(__brev((unsigned)t) >> (32 - LB)) : 0;  // brev(t)
-    // parameter copies by warps 2 and 3 (warp 0 issues the table copies first)
+    // parameter copies by warps 2 and 3 (warp 0 issues the table copies first).  The kernel parameter
+    // is __grid_constant__, so these loops read it in place through generic pointers: one round of
+    // loads in parallel.  Written as copies with constant indices (a chain of predicated constant-bank
+    // reads), they cost 1.8 us per frame in a several-frames launch and 1.7 us back to back with B in
+    // the L2 (the parameter lines miss once the kernel's code has streamed through the SM's caches).
     if (warp == 2) {
-#pragma unroll
-        for (int i = 0; i < SAFR_MAX_G; ++i)
-            if (lane == (i & 31)) s_star_tt[i] = fp.star_tt[i];
+        for (int i = lane; i < SAFR_MAX_G; i += 32) s_star_tt[i] = fp.star_tt[i];
     } else if (warp == 3) {
-#pragma unroll
-        for (int gi = 0; gi < 2; ++gi) {
-            if (lane == 0) {
-                s_grp[gi].G = fp.grp[gi].G;
-                s_grp[gi].b_row0 = fp.grp[gi].b_row0;
-                s_grp[gi].resample = fp.grp[gi].resample;
-            }
-#pragma unroll
-            for (int q = 0; q < SAFR_MAX_GROUP_G; ++q)
-                if (lane == q) s_grp[gi].star[q] = fp.grp[gi].star[q];
-        }
+        const int *src = reinterpret_cast<const int *>(&fp.grp[0]);
+        int *dst = reinterpret_cast<int *>(&s_grp[0]);
+        constexpr int NWD = (int)(2 * sizeof(GroupDev) / sizeof(int));
+        for (int i = lane; i < NWD; i += 32) dst[i] = src[i];
     }
     unsigned long long *stamp = fp.stamps ? fp.stamps + (size_t)b * SAFR_TRACE_MARKS : nullptr;
 #define SAFR_MARK(n, cond)                                   \
@@ -1133,7 +1128,7 @@ __device__ __forceinline__ void bar_count_advance(unsigned long long *bar, unsig
 // may begin at once (its CTAs take the SMs this frame's CTAs leave, and it waits for this frame to
 // finish before it touches its data).
 template <int M, typename R, typename TIN, typename TOUT, int CK = 1>
-__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R> fp)
+__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(const __grid_constant__ Frame2Params<R> fp)
 {
     pdl_trigger();
     unsigned long long base = 0;
@@ -1150,7 +1145,7 @@ __global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2(Frame2Params<R>
 // column phase, their only reader; it writes the layer spectra after its own first grid barrier,
 // which a CTA passes only once every CTA is done with frame f's last phase, their only reader.
 template <int M, typename R, typename TIN, typename TOUT, int CK = 1>
-__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2_frames(Frame2Params<R> fp, int nframes)
+__global__ void __launch_bounds__(frame2_threads(M), 1) k_frame2_frames(const __grid_constant__ Frame2Params<R> fp, int nframes)
 {
     pdl_trigger();
     unsigned long long base = 0;
