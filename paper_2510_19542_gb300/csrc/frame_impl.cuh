@@ -11,11 +11,12 @@
 // all data in registers, lanes exchanged by shuffles.
 //
 //   prologue  per-lane twiddles and this CTA's later-phase tables are loaded
-//             into registers; the CTA's first B column block (all groups,
-//             layers and stars; contiguous) is copied into shared memory by
-//             TMA (cp.async.bulk) and lands during phase 1; B of every column
-//             after this CTA's first goes to L2 by bulk prefetch;
-//   phase 1   one transform per row pair of the zero-padded wavefronts
+//             into registers; B of every column after this CTA's first goes
+//             to L2 by bulk prefetch;
+//   phase 1   once warp 0 has issued its wavefront loads, the CTA's first B
+//             column block (all groups, layers and stars; contiguous) is
+//             copied into shared memory by TMA (cp.async.bulk);
+//             one transform per row pair of the zero-padded wavefronts
 //             (Section 2): rows a0, a0 + 1 packed as z = psi_a0 + i psi_a0+1,
 //             forward FFT along q, split into the two half spectra
 //             -> w1[g][k][p] (k < M/2).  LGS rows of a mixed plan also give
@@ -386,10 +387,10 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             tma_load_1d(ti0, fp.rs_i0 + (size_t)l * M, ib, &mbar_t);
             tma_load_1d(tfw, fp.rs_w + (size_t)l * M, wb, &mbar_t);
         }
-        // this CTA's first B column block: it lands during phase 1, so phase 1's stores and the
-        // first grid barrier do not queue behind the 21 MB stream (issued after the frame data
-        // had landed instead, it held the first barrier back by about 1 us)
-        if (fp.stage_b && b < Mh) copy_b(b);
+        // this CTA's first B column block is copied in phase 1, right after warp 0 has issued its
+        // wavefront loads: issued here, the 21 MB stream (from HBM when B is not in the L2) delayed
+        // the frame data by about 2.4 us; issued after the frame data had landed, it held the first
+        // grid barrier back (a release at GPU scope waits for the CTA's bulk copies in flight)
     }
     // every thread waits for the tables before its first transform (no thread leaves
     // on a timeout here: the status word records it and the barriers stay balanced)
@@ -416,7 +417,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
     __syncthreads();  // the parameter copies
     SAFR_MARK(1, true);
 
-    tma_pending = fp.stage_b && b < Mh;  // the B block copy issued above
+    tma_pending = fp.stage_b && b < Mh;  // the B block copy, issued in phase 1 before any early return
     // leave early (timeout or test hook) only after this CTA's own bulk copy landed
     auto drain = [&]() {
         if (tma_pending) mbar_wait_bounded(&mbar, bph, fp.timeout_ns, fp.status);
@@ -473,6 +474,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                             m1[r] = mb1[qc >> 5];
                         }
                     }
+                    if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);  // B after this warp's loads
 #pragma unroll
                     for (int r = 0; r < RR; ++r) {
                         const int qq = t + LW * r - o;
@@ -508,6 +510,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
                                 m1[u] = mb1[qc >> 5];
                             }
                         }
+                        if (r0 == 0 && first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);  // B after the first batch
 #pragma unroll
                         for (int u = 0; u < RB; ++u) {
                             const int r = r0 + u, qq = t + LW * r - o;
@@ -579,6 +582,7 @@ __device__ __forceinline__ bool frame_body(const Frame2Params<R> &fp, unsigned l
             first = false;
         }
         if (first) tables();  // a warp without phase-1 rows
+        if (first && tid == 0 && fp.stage_b && b < Mh) copy_b(b);  // warp 0 had no rows
     }
     if (b == fp.skip_cta) {  // test hook: every other CTA's first barrier must time out
         drain();
